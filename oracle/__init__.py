@@ -1,0 +1,44 @@
+"""FP64 CPU oracle for the improved-staggered even-odd solve (test infrastructure).
+
+This package is test infrastructure.  Only the tests, the smoke check and the
+benchmark's CPU-baseline leg may import it; the library never does, and the
+library shares no code with it (no kernels, helpers, tables or constants).
+It is plain numpy in float64/complex128, written for a reader to check
+against the definitions by eye, not for speed.
+
+Parity status of each function (what pins it, checked by the CPU tests):
+  * dslash / apply_m       -- free-field closed form on plane waves,
+                              anti-hermiticity D_eo = -D_oe^dag, gauge
+                              covariance under random SU(3) transforms, full
+                              free-field spectrum of a dense 4^4 build.
+  * cg                     -- dense LU solve (numpy.linalg.solve) on 4^4.
+  * multishift_cg          -- dense LU solve per shift on 4^4, and single-mass
+                              CG run shift by shift.
+  * true_residual          -- exact definition ||b - M x|| / ||b||.
+"""
+
+from .staggered import (
+    staggered_phase,
+    site_coords,
+    parity_sites,
+    neighbour_lex,
+    dslash,
+    apply_m,
+    true_residual,
+    cg,
+    multishift_cg,
+    dense_matrix,
+)
+
+__all__ = [
+    "staggered_phase",
+    "site_coords",
+    "parity_sites",
+    "neighbour_lex",
+    "dslash",
+    "apply_m",
+    "true_residual",
+    "cg",
+    "multishift_cg",
+    "dense_matrix",
+]
