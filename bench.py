@@ -1,0 +1,500 @@
+"""Benchmark: 32^4 improved-staggered even-odd CG to 1e-10, mixed vs plain FP64.
+
+Workload (the paper's staggered CG, Sec. 4.1, on a synthetic stand-in for its
+equilibrated ensembles): 32^4 lattice, thin links exp(0.3 i H) reunitarised,
+fat = U + 1/8 staples, Naik = -1/24 UUU, periodic, m = 0.01, 4 seeded
+Gaussian even-site sources, FP64 true relative residual 1e-10.
+
+A step solves all 4 sources with the chosen solver (stag_cg through the C
+ABI, inputs resident in HBM).  `value` is seconds per source solve.  The
+same JSON line carries the plain FP64 CG time, the Dslash roofline (device
+time of the dominant kernel per launch, measured with CUDA events on its
+launch stream during the timed region), the end-to-end time with host
+buffers, the oracle's CPU time on a bounded sample, and the SM clocks seen.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash HBM GB/s (% peak); 32^4 CG secs to 1e-10 rel. residual, plain vs chosen"
+DIMS = (32, 32, 32, 32)
+EPS = 0.3
+MASS = 0.01
+NSRC = 4
+TOL = 1e-10
+GAUGE_SEED = 1000
+SOURCE_SEEDS = [5000 + k for k in range(NSRC)]
+CHOSEN = "mixed32"
+RECON = 12
+FLOP_PER_SITE = 1146
+# algorithmic bytes per output site of one Dslash: 16 link matrices (8 fat x
+# 9 complex + 8 Naik x NL complex) read once, the input vector read once,
+# the output written once
+ELEM_BYTES = {"fp64": 16, "fp32": 8, "fp16": 4, "fx16": 4}
+VEC_BYTES = {"fp64": 48, "fp32": 24, "fp16": 16, "fx16": 16}
+MODE_PREC = {"plain64": "fp64", "mixed32": "fp32", "mixed16": "fp16", "mixedfx16": "fx16"}
+
+
+def dslash_bytes_per_site(prec, recon):
+    nl = 6 if (recon == 12 and prec != "fp64") else 9
+    return (8 * 9 + 8 * nl) * ELEM_BYTES[prec] + 2 * VEC_BYTES[prec]
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("dslash_impl.cuh", "common.cuh", "links.cu"):
+        with open(os.path.join(ROOT, "paper_1712_00143_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_id):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "dslash_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    ent = d.get(kernel_id)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------ clocks
+REASON_BITS = {
+    0x1: "gpu_idle",
+    0x2: "applications_clocks_setting",
+    0x4: "sw_power_cap",
+    0x8: "hw_slowdown",
+    0x20: "sw_thermal_slowdown",
+    0x40: "hw_thermal_slowdown",
+    0x80: "hw_power_brake_slowdown",
+    0x100: "display_clock_setting",
+}
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        cmd = [
+            "nvidia-smi",
+            f"--id={self.index}",
+            "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,utilization.gpu",
+            "--format=csv,noheader,nounits",
+            "-lms",
+            "200",
+        ]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 4:
+                continue
+            try:
+                sm, smax = float(parts[0]), float(parts[1])
+                reasons = int(parts[2], 16) if parts[2].startswith("0x") else int(parts[2])
+                util = float(parts[3])
+            except ValueError:
+                continue
+            self.samples.append((sm, smax, reasons, util))
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        loaded = [s for s in self.samples if s[3] >= 50] or self.samples
+        reasons = 0
+        for s in loaded:
+            reasons |= s[2]
+        names = [n for b, n in REASON_BITS.items() if reasons & b and n != "gpu_idle"]
+        return {
+            "sm_mhz": statistics.median(s[0] for s in loaded),
+            "sm_max_mhz": max(s[1] for s in self.samples),
+            "reasons": names,
+            "samples": len(loaded),
+        }
+
+
+# ------------------------------------------------------------------ distributed harness
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def reduce_max(value, world):
+    """Max over ranks of a float (identity for a single process)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ inputs
+def make_inputs():
+    import synth
+
+    fat, lng = synth.gauge_field(DIMS, EPS, GAUGE_SEED)
+    srcs = [synth.gaussian_source(DIMS, s) for s in SOURCE_SEEDS]
+    return fat, lng, srcs
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+def cpu_baseline(fat, lng, b, iters_full, sample_iters=3):
+    """The FP64 numpy oracle, timed on a bounded sample and scaled to a solve.
+
+    Runs `sample_iters` oracle CG iterations (each one operator application
+    plus vector updates) and one true-residual application, and scales the
+    time per application to the `iters_full` iterations of a full solve."""
+    import oracle
+
+    t = time.perf_counter()
+    oracle.cg(fat, lng, b, MASS, DIMS, tol=TOL, max_iter=sample_iters)
+    el = time.perf_counter() - t
+    per = el / (sample_iters + 1)
+    return {
+        "value": per * (iters_full + 1),
+        "unit": "s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": f"{sample_iters} FP64 CG iterations of the numpy oracle on 32^4 source 0 "
+        f"({el:.1f} s), scaled to the {iters_full} iterations of a full FP64 solve",
+    }
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_1712_00143_gb300 as stag
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    fat, lng, srcs = make_inputs()
+    h = stag.stag_load_links(DIMS, torch.from_numpy(fat).to(dev), torch.from_numpy(lng).to(dev), recon_long=RECON)
+    bs = [torch.from_numpy(b).to(dev) for b in srcs]
+    xs = [torch.zeros_like(b) for b in bs]
+    stream = torch.cuda.current_stream()
+    Vh = h.Vh
+
+    def step(mode):
+        infos = []
+        for x, b in zip(xs, bs):
+            infos.append(stag.stag_cg(h, x, b, MASS, mode=mode, tol=TOL))
+        return infos
+
+    # plain FP64 reference solve (one pass over the sources, after one warm-up)
+    step("plain64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_infos = step("plain64")
+    torch.cuda.synchronize()
+    plain_s = (time.perf_counter() - t0) / NSRC
+
+    for _ in range(args.warmup):
+        step(CHOSEN)
+    torch.cuda.synchronize()
+
+    stag.stag_profile_reset()
+    stag.stag_profile_enable(True)
+    launches0 = stag.stag_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos_all = []
+    with ClockSampler(local_rank) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos_all += step(CHOSEN)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        barrier(world)
+    launches = stag.stag_launch_count() - launches0
+    n_d, ms_d = stag.stag_profile_read("dslash")
+    n_e, ms_e = stag.stag_profile_read("dslash_epi")
+    stag.stag_profile_enable(False)
+    ms_total = reduce_max(e0.elapsed_time(e1), world)
+    ms_per_step = ms_total / args.steps
+    value = ms_per_step / 1e3 / NSRC
+
+    # end to end through the C ABI with host buffers: H2D of the sources and
+    # D2H of the solutions inside the timed region
+    hb = [torch.from_numpy(b).pin_memory() for b in srcs]
+    hx = [torch.empty_like(b) for b in hb]
+    hx = [t.pin_memory() for t in hx]
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, min(args.steps, 3))):
+        for k in range(NSRC):
+            bd = hb[k].to(dev, non_blocking=True)
+            xd = torch.zeros_like(bd)
+            stag.stag_cg(h, xd, bd, MASS, mode=CHOSEN, tol=TOL)
+            hx[k].copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = reduce_max((time.perf_counter() - t0) / max(1, min(args.steps, 3)) / NSRC, world)
+    vec_bytes = Vh * 3 * 16
+
+    # verify every timed solve
+    ok = all(i["converged"] and i["true_rel_resid"] <= TOL for i in infos_all + plain_infos)
+    prec = MODE_PREC[CHOSEN]
+    per_launch_ms = ms_d / max(n_d, 1)
+    bytes_launch = dslash_bytes_per_site(prec, RECON) * Vh
+    achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    kernel_id = f"k_dslash<{ {'fp32': 32, 'fp16': 16, 'fx16': 15, 'fp64': 64}[prec] },{6 if RECON == 12 else 9}>"
+    traffic = ncu_traffic(kernel_id)
+    iters = [i["iters"] for i in infos_all[:NSRC]]
+    iters_plain = [i["iters"] for i in plain_infos]
+
+    result = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(fat, lng, srcs[0], iters_plain[0])
+        clocks = clk.summary()
+        result = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_per_step,
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": "32^4 even-odd improved-staggered CG, m=0.01, eps=0.3, 4 Gaussian sources, "
+                "1e-10 FP64 true residual",
+                "solver": CHOSEN,
+                "link_storage": f"{prec}, Naik recon {RECON}",
+                "sources_per_step": NSRC,
+                "l2": "inputs larger than L2 (links 0.5-1.2 GB per precision)",
+                "parallelism": "replicas" if world > 1 else "single GPU",
+            },
+            "plain_fp64": {"value": plain_s, "unit": "s", "iters": iters_plain},
+            "speedup_vs_plain": plain_s / value,
+            "iters": iters,
+            "all_converged": ok,
+            "roofline": {
+                "bound": "hbm",
+                "kernel": kernel_id,
+                "achieved": achieved,
+                "peak": peak,
+                "peak_kind": peak_kind,
+                "unit": "GB/s",
+                "frac": achieved / peak,
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": bytes_launch,
+                "launches": n_d,
+                "avg_launch_us": per_launch_ms * 1e3,
+                "gflops": FLOP_PER_SITE * Vh / (per_launch_ms * 1e-3) / 1e9,
+                "epilogue_variant_avg_us": ms_e / max(n_e, 1) * 1e3,
+            },
+            "e2e": {
+                "value": e2e_s,
+                "unit": "s",
+                "h2d_bytes_per_step": NSRC * vec_bytes,
+                "d2h_bytes_per_step": NSRC * vec_bytes,
+            },
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+    h.free()
+    return result
+
+
+# ------------------------------------------------------------------ reference arm (oracle)
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle  # noqa: F401
+
+    fat, lng, srcs = make_inputs()
+    iters_full = ORACLE_FULL_ITERS
+    times = []
+    for k in range(args.warmup + args.steps):
+        c = cpu_baseline(fat, lng, srcs[0], iters_full, sample_iters=2)
+        if k >= args.warmup:
+            times.append(c["value"])
+    v = statistics.mean(times)
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": v,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": v * NSRC * 1e3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": "32^4 even-odd improved-staggered CG, m=0.01, eps=0.3, 4 Gaussian sources, "
+            "1e-10 FP64 true residual",
+            "solver": "FP64 numpy oracle",
+        },
+        "cpu_baseline": dict(c, value=v),
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+# Iterations the FP64 oracle's own CG needs to reach 1e-10 on the bench
+# workload (source 0), measured by running the oracle to convergence once.
+ORACLE_FULL_ITERS = 487
+
+
+def run_dslash_sweep(args):
+    """Dslash bandwidth sweep over lattice sizes, storage formats and Naik
+    storage (the paper's single-GPU L^4 sweep, Sec. 4.1, Fig. 9): one JSON
+    line per case with the kernel's device time per launch (CUDA events on
+    its launch stream), algorithmic GB/s, GFLOP/s at 1146 flop/site and the
+    fraction of the measured HBM bandwidth."""
+    import torch
+
+    import paper_1712_00143_gb300 as stag
+    import synth
+
+    peak, peak_kind = measured_peaks()
+    for L in args.sweep_dims:
+        dims = tuple(int(v) for v in L.split("x")) if "x" in L else (int(L),) * 4
+        fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
+        fd, ld = torch.from_numpy(fat).cuda(), torch.from_numpy(lng).cuda()
+        del fat, lng
+        psi = torch.from_numpy(synth.random_spinor(dims, 3)).cuda()
+        out = torch.empty_like(psi)
+        for recon in args.sweep_recons:
+            for prec in args.sweep_precs:
+                if prec == "fp64" and recon == 12:
+                    continue
+                h = stag.stag_load_links(dims, fd, ld, recon_long=recon, prec_mask=1 << stag.PREC[prec])
+                for _ in range(3):
+                    stag.stag_dslash(h, out, psi, 1, prec)
+                torch.cuda.synchronize()
+                stag.stag_profile_reset()
+                stag.stag_profile_enable(True)
+                for _ in range(args.sweep_reps):
+                    stag.stag_dslash(h, out, psi, 1, prec)
+                n, ms = stag.stag_profile_read("dslash")
+                stag.stag_profile_enable(False)
+                per = ms / max(n, 1)
+                byt = dslash_bytes_per_site(prec, recon) * h.Vh
+                gbs = byt / (per * 1e-3) / 1e9
+                print(json.dumps({"dslash": "x".join(map(str, dims)), "prec": prec, "recon": recon,
+                                  "us": per * 1e3, "GB/s": gbs, "frac": gbs / peak, "peak_kind": peak_kind,
+                                  "GFLOP/s": FLOP_PER_SITE * h.Vh / (per * 1e-3) / 1e9,
+                                  "bytes_per_launch": byt}), flush=True)
+                h.free()
+        del fd, ld, psi, out
+        torch.cuda.empty_cache()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dslash-sweep", action="store_true", help="Dslash bandwidth sweep instead of the solve")
+    ap.add_argument("--sweep-dims", nargs="+", default=["8", "16", "24", "32", "40", "48", "48x48x48x96"])
+    ap.add_argument("--sweep-precs", nargs="+", default=["fp64", "fp32", "fp16", "fx16"])
+    ap.add_argument("--sweep-recons", nargs="+", type=int, default=[18, 12])
+    ap.add_argument("--sweep-reps", type=int, default=20)
+    args = ap.parse_args(argv)
+    if args.dslash_sweep:
+        run_dslash_sweep(args)
+        return
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        # the oracle runs on rank 0's host cores only; other ranks do no work
+        res = run_reference(args, rank, world) if rank == 0 else None
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="nccl")
+    res = run_gpu(args, rank, world, local_rank)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

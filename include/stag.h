@@ -1,0 +1,170 @@
+/*
+ * stag.h -- C ABI of libstag, a single-GPU (GB300, sm_103a) library for the
+ * even-odd improved-staggered conjugate-gradient solve.
+ *
+ * What it computes (the paper benchmarks the staggered single-mass and
+ * multi-shift CG, Sec. 1 and Sec. 4.1, but prints no operator; the standard
+ * improved-staggered form it refers to is written out here):
+ *
+ *   (D psi)(x) = 1/2 sum_mu eta_mu(x) [ F_mu(x) psi(x+mu) - F_mu(x-mu)^+ psi(x-mu)
+ *                                      + L_mu(x) psi(x+3mu) - L_mu(x-3mu)^+ psi(x-3mu) ]
+ *
+ *   eta_x = 1, eta_y = (-1)^x, eta_z = (-1)^(x+y), eta_t = (-1)^(x+y+z),
+ *   periodic wrap in all directions, F = fat links, L = Naik (long) links,
+ *   M = m^2 - D_eo D_oe on even sites (Hermitian positive definite).
+ *
+ * Canonical layout (the only layout callers see):
+ *   - extents dims[4] = {Lx, Ly, Lz, Lt}, each even and >= 4;
+ *   - sites lexicographic, x fastest: lex = x + Lx*(y + Ly*(z + Lz*t));
+ *   - links: [V][4][3][3] interleaved complex double (re, im), mu = x,y,z,t,
+ *     row-major colour matrices, WITHOUT staggered phases or the 1/2 (the
+ *     library folds both in);
+ *   - single-parity colour-vector fields: [V/2][3] complex double indexed by
+ *     lex/2; an even field lives on sites with (x+y+z+t) even.
+ *   - several right-hand sides: [nrhs][V/2][3], each system contiguous.
+ *
+ * Pointers: every field/link pointer is a DEVICE pointer (cudaMalloc or a
+ * PyTorch CUDA tensor) unless stated otherwise.  The caller owns them.
+ * stream: a cudaStream_t passed as void*; NULL means the legacy default
+ * stream.  Solvers synchronise `stream` before returning; stag_dslash and
+ * stag_apply_m are asynchronous.
+ *
+ * Errors: every call returns an int status (0 = STAG_OK, negative = error);
+ * no exception crosses the ABI.  A handle is not thread-safe: use one handle
+ * per host thread, or serialise calls on it.
+ */
+#ifndef STAG_H
+#define STAG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define STAG_OK 0
+#define STAG_EINVAL (-1)      /* null pointer, odd or too small extent, bad enum */
+#define STAG_ENOMEM (-2)      /* device allocation failed */
+#define STAG_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed */
+#define STAG_ENOTCONV (-4)    /* max_iter reached; x holds the last iterate */
+#define STAG_EBREAKDOWN (-5)  /* NaN/Inf or <p,Ap> <= 0 in a solver */
+#define STAG_ENOTUNITARY (-6) /* recon-12 asked for links with L/c3 not in SU(3) */
+#define STAG_ETIMEOUT (-7)    /* a bounded device wait gave up */
+
+/* --------------------------------------------------------------- precision */
+/* STAG_FP16: IEEE binary16 storage.  STAG_FX16: 16-bit fixed point (15
+ * fraction bits) in units of a per-site (vectors) or per-field (links) scale.
+ * Both keep one FP32 scale per site for vectors and compute in FP32. */
+typedef enum { STAG_FP64 = 0, STAG_FP32 = 1, STAG_FP16 = 2, STAG_FX16 = 3 } stag_prec;
+
+/* Solver modes.  PLAIN64: every operation in FP64.  MIXED32 / MIXED16 /
+ * MIXEDFX16: the Krylov iteration uses the FP32 / binary16 / 16-bit
+ * fixed-point Dslash and search direction, FP32 residual and iterate, FP64
+ * reductions, FP64 solution accumulation and FP64 "reliable updates" (true
+ * residual b - M y recomputed in FP64 whenever the iterated residual has
+ * dropped by `delta` since the last update). */
+typedef enum { STAG_PLAIN64 = 0, STAG_MIXED32 = 1, STAG_MIXED16 = 2, STAG_MIXEDFX16 = 3 } stag_mode;
+
+typedef struct stag_lattice_s* stag_lattice_t; /* opaque, library-owned */
+
+typedef struct {
+  int recon_long;    /* 18: long links stored in full; 12: two rows stored, the
+                        third rebuilt as conj(row0 x row1) (FP32 and 16-bit
+                        copies; needs L/long_coeff in SU(3), else ENOTUNITARY) */
+  double long_coeff; /* c3 with L = c3 * (product of SU(3) links); -1/24 */
+  unsigned prec_mask; /* bit (1 << stag_prec) per copy to build; 0 = all four */
+} stag_link_opts;
+
+typedef struct {
+  double tol;          /* target ||b - M x|| / ||b|| (FP64 true residual) */
+  int max_iter;        /* cap on Krylov iterations (per solve / per shift) */
+  int mode;            /* stag_mode */
+  double delta;        /* reliable-update trigger: ||r|| < delta * max||r|| */
+  int use_initial_guess; /* 1: start from the x passed in; 0: from zero */
+  int check_interval;  /* iterations between host convergence checks (>=1) */
+  double ms_tol;       /* multi-shift: relative residual at which the shared
+                          Krylov loop hands each shift to refinement (<=0: tol) */
+} stag_solve_params;
+
+typedef struct {
+  int iters;            /* Krylov iterations (multi-shift: shared + refinement) */
+  int reliable_updates; /* FP64 true-residual recomputations */
+  int converged;        /* 1 if true_rel_resid <= tol */
+  int status;           /* STAG_OK or the error for this system */
+  double true_rel_resid; /* ||b - M x|| / ||b|| recomputed in FP64 on the GPU */
+  double seconds;       /* wall time of the solve on the host */
+} stag_solve_info;
+
+/* Default parameters: tol 1e-10, max_iter 100000, MIXED32, delta 0.1,
+ * check_interval 16, ms_tol 1e-6. */
+void stag_default_params(stag_solve_params* p);
+
+/* Load a gauge field (the operator's fat and long links) into a new handle.
+ * Builds, on the GPU, the library's internal site-blocked structure-of-arrays
+ * copies (the paper's QPhiX uses an SOA layout, Sec. 3) with the staggered
+ * phases and the 1/2 folded in, in each precision of opts->prec_mask.
+ *   out  : receives the handle (release with stag_free_lattice).
+ *   dims : host array {Lx, Ly, Lz, Lt}, even, each >= 4.
+ *   fat, lng : device, canonical [V][4][3][3] complex double.  Copied; the
+ *          caller may free them after the call returns.
+ *   opts : may be NULL (recon 18, c3 = -1/24, all precisions).
+ * Errors: EINVAL, ENOMEM, ECUDA, ENOTUNITARY.  Synchronises `stream`. */
+int stag_load_links(stag_lattice_t* out, const int dims[4], const void* fat, const void* lng,
+                    const stag_link_opts* opts, void* stream);
+
+int stag_free_lattice(stag_lattice_t lat);
+
+/* Lattice extents and the per-parity site count V/2 of a handle. */
+int stag_lattice_info(stag_lattice_t lat, int dims[4], long long* vh);
+
+/* out = D psi restricted to sites of parity out_parity (0 even, 1 odd);
+ * in lives on the other parity.  Computed with the links and arithmetic of
+ * `prec` (FP64: FP64 throughout; FP32: FP32 storage and accumulation; FP16
+ * and FX16: 16-bit storage with a per-site vector scale and a per-field link
+ * scale, FP32 accumulation).  in/out: device, canonical [nrhs][V/2][3] complex double
+ * (converted to and from the internal layout around the kernel).
+ * Asynchronous on `stream`.  Errors: EINVAL, ENOMEM, ECUDA. */
+int stag_dslash(stag_lattice_t lat, void* out, const void* in, int out_parity, int prec, int nrhs,
+                void* stream);
+
+/* out = (m^2 + shift) in - D_eo D_oe in on even sites, arithmetic of `prec`.
+ * in/out: device canonical [V/2][3] complex double.  Asynchronous. */
+int stag_apply_m(stag_lattice_t lat, void* out, const void* in, double mass, double shift, int prec,
+                 void* stream);
+
+/* Solve M x = b (even sites) to params->tol in FP64 true residual.
+ * x, b: device canonical [V/2][3] complex double; x is read as the initial
+ * guess when params->use_initial_guess, and always written.
+ * info: host, may be NULL.  Returns STAG_OK, ENOTCONV (x = last iterate),
+ * EBREAKDOWN, EINVAL, ENOMEM, ECUDA.  Synchronises `stream`. */
+int stag_cg(stag_lattice_t lat, void* x, const void* b, double mass, const stag_solve_params* params,
+            stag_solve_info* info, void* stream);
+
+/* Solve (M + shifts[s]) x_s = b for nshift shifts from one shared Krylov
+ * space (multi-shift CG, the production workhorse of Sec. 4.1), then refine
+ * each shift whose FP64 true residual misses tol with single-shift CG from
+ * x_s in the same mode.  x: host array of nshift device pointers
+ * (canonical [V/2][3] complex double); shifts: host array, each >= 0.
+ * infos: host array of nshift, may be NULL.  Synchronises `stream`. */
+int stag_multishift_cg(stag_lattice_t lat, void* const* x, const void* b, double mass,
+                       const double* shifts, int nshift, const stag_solve_params* params,
+                       stag_solve_info* infos, void* stream);
+
+/* Human-readable text of a status code (static storage). */
+const char* stag_strerror(int status);
+
+/* ---------------------------------------------------------- instrumentation
+ * When enabled, every kernel the library launches is bracketed by a pair of
+ * CUDA events recorded on its launch stream; stag_profile_read returns, for
+ * a kernel family name ("dslash", "dslash_epilogue", "blas", "reduce",
+ * "convert", "links"), the number of launches and their summed device time
+ * (ms).  stag_launch_count counts all library kernel launches since the last
+ * reset, whether or not profiling is on. */
+int stag_profile_enable(int on);
+int stag_profile_reset(void);
+int stag_profile_read(const char* family, long long* launches, double* total_ms);
+long long stag_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STAG_H */

@@ -1,0 +1,289 @@
+"""Python binding of libstag, the GB300 (sm_103a) even-odd improved-staggered solver library.
+
+The functions carry the C ABI's names (``include/stag.h``) and only marshal
+arguments: PyTorch CUDA tensors become device pointers and the current
+PyTorch stream becomes the ``cudaStream_t``.  Every step of the computation
+runs in the library's own CUDA kernels; there is no CPU fallback, and
+importing this package fails loudly if ``libstag.so`` has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``).
+
+Field tensors are complex128 CUDA tensors in the canonical layout: links
+``[V][4][3][3]``, single-parity colour vectors ``[V/2][3]`` (or
+``[nrhs][V/2][3]``), sites lexicographic with x fastest, a parity field
+indexed by lex // 2.
+"""
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstag.so")
+
+STAG_OK = 0
+STAG_EINVAL = -1
+STAG_ENOMEM = -2
+STAG_ECUDA = -3
+STAG_ENOTCONV = -4
+STAG_EBREAKDOWN = -5
+STAG_ENOTUNITARY = -6
+STAG_ETIMEOUT = -7
+
+STAG_FP64, STAG_FP32, STAG_FP16, STAG_FX16 = 0, 1, 2, 3
+STAG_PLAIN64, STAG_MIXED32, STAG_MIXED16, STAG_MIXEDFX16 = 0, 1, 2, 3
+
+PREC = {"fp64": STAG_FP64, "fp32": STAG_FP32, "fp16": STAG_FP16, "fx16": STAG_FX16}
+MODE = {"plain64": STAG_PLAIN64, "mixed32": STAG_MIXED32, "mixed16": STAG_MIXED16, "mixedfx16": STAG_MIXEDFX16}
+
+# every entry point declared in include/stag.h
+EXPORTS = (
+    "stag_default_params",
+    "stag_load_links",
+    "stag_free_lattice",
+    "stag_lattice_info",
+    "stag_dslash",
+    "stag_apply_m",
+    "stag_cg",
+    "stag_multishift_cg",
+    "stag_strerror",
+    "stag_profile_enable",
+    "stag_profile_reset",
+    "stag_profile_read",
+    "stag_launch_count",
+)
+
+
+class StagError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} ({status})")
+
+
+class LinkOpts(ctypes.Structure):
+    _fields_ = [("recon_long", ctypes.c_int), ("long_coeff", ctypes.c_double), ("prec_mask", ctypes.c_uint)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("mode", ctypes.c_int),
+        ("delta", ctypes.c_double),
+        ("use_initial_guess", ctypes.c_int),
+        ("check_interval", ctypes.c_int),
+        ("ms_tol", ctypes.c_double),
+    ]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("reliable_updates", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("true_rel_resid", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: the CUDA library must be built first "
+            '(python -c "import __graft_entry__ as g; g.build()")'
+        )
+    lib = ctypes.CDLL(path)
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "stag_default_params": (None, [ctypes.POINTER(SolveParams)]),
+        "stag_load_links": (ci, [ctypes.POINTER(vp), ctypes.POINTER(ci), vp, vp, ctypes.POINTER(LinkOpts), vp]),
+        "stag_free_lattice": (ci, [vp]),
+        "stag_lattice_info": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_longlong)]),
+        "stag_dslash": (ci, [vp, vp, vp, ci, ci, ci, vp]),
+        "stag_apply_m": (ci, [vp, vp, vp, cd, cd, ci, vp]),
+        "stag_cg": (ci, [vp, vp, vp, cd, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), vp]),
+        "stag_multishift_cg": (
+            ci,
+            [vp, ctypes.POINTER(vp), vp, cd, ctypes.POINTER(cd), ci, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), vp],
+        ),
+        "stag_strerror": (ctypes.c_char_p, [ci]),
+        "stag_profile_enable": (ci, [ci]),
+        "stag_profile_reset": (ci, []),
+        "stag_profile_read": (ci, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(cd)]),
+        "stag_launch_count": (ctypes.c_longlong, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def strerror(status):
+    return _lib.stag_strerror(int(status)).decode()
+
+
+def _check(status, where):
+    if status != STAG_OK:
+        raise StagError(status, where)
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t, name, numel=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda or t.dtype != torch.complex128 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _prec(p):
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def default_params(**kw):
+    p = SolveParams()
+    _lib.stag_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "mode" and isinstance(v, str):
+            v = MODE[v]
+        setattr(p, k, v)
+    return p
+
+
+class LatticeHandle:
+    """Owns a ``stag_lattice_t``; released by :func:`stag_free_lattice` or on GC."""
+
+    def __init__(self, ptr, dims):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.dims = tuple(dims)
+        V = 1
+        for d in dims:
+            V *= d
+        self.V = V
+        self.Vh = V // 2
+
+    def free(self):
+        if self.ptr and self.ptr.value:
+            _check(_lib.stag_free_lattice(self.ptr), "stag_free_lattice")
+            self.ptr = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def stag_load_links(dims, fat, lng, recon_long=18, long_coeff=-1.0 / 24.0, prec_mask=0, stream=None):
+    """Copy canonical fat/long links into a new lattice handle (see stag.h)."""
+    dims = tuple(int(d) for d in dims)
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*dims)
+    o = LinkOpts(int(recon_long), float(long_coeff), int(prec_mask))
+    st = _lib.stag_load_links(
+        ctypes.byref(h), d, _ptr(fat, "fat", V * 36), _ptr(lng, "lng", V * 36), ctypes.byref(o), _stream(stream)
+    )
+    _check(st, "stag_load_links")
+    return LatticeHandle(h.value, dims)
+
+
+def stag_free_lattice(h):
+    h.free()
+
+
+def stag_lattice_info(h):
+    d = (ctypes.c_int * 4)()
+    vh = ctypes.c_longlong()
+    _check(_lib.stag_lattice_info(h.ptr, d, ctypes.byref(vh)), "stag_lattice_info")
+    return tuple(d), vh.value
+
+
+def stag_dslash(h, out, inp, out_parity, prec="fp64", nrhs=1, stream=None):
+    """out = D inp on parity out_parity (canonical [nrhs][V/2][3] complex128)."""
+    n = h.Vh * 3 * nrhs
+    st = _lib.stag_dslash(
+        h.ptr, _ptr(out, "out", n), _ptr(inp, "inp", n), int(out_parity), _prec(prec), int(nrhs), _stream(stream)
+    )
+    _check(st, "stag_dslash")
+    return out
+
+
+def stag_apply_m(h, out, inp, mass, shift=0.0, prec="fp64", stream=None):
+    """out = (m^2 + shift) inp - D_eo D_oe inp on even sites."""
+    n = h.Vh * 3
+    st = _lib.stag_apply_m(
+        h.ptr, _ptr(out, "out", n), _ptr(inp, "inp", n), float(mass), float(shift), _prec(prec), _stream(stream)
+    )
+    _check(st, "stag_apply_m")
+    return out
+
+
+def stag_cg(h, x, b, mass, params=None, stream=None, raise_on_error=True, **kw):
+    """Solve M x = b; returns the solve info as a dict (status included)."""
+    p = params if params is not None else default_params(**kw)
+    info = SolveInfo()
+    n = h.Vh * 3
+    st = _lib.stag_cg(h.ptr, _ptr(x, "x", n), _ptr(b, "b", n), float(mass), ctypes.byref(p), ctypes.byref(info), _stream(stream))
+    if raise_on_error and st not in (STAG_OK,):
+        raise StagError(st, "stag_cg")
+    d = info.as_dict()
+    d["return"] = st
+    return d
+
+
+def stag_multishift_cg(h, xs, b, mass, shifts, params=None, stream=None, raise_on_error=True, **kw):
+    """Solve (M + shifts[s]) xs[s] = b for all shifts; returns a list of info dicts."""
+    p = params if params is not None else default_params(**kw)
+    ns = len(shifts)
+    n = h.Vh * 3
+    ptrs = (ctypes.c_void_p * ns)(*[_ptr(x, f"xs[{i}]", n).value for i, x in enumerate(xs)])
+    sh = (ctypes.c_double * ns)(*[float(s) for s in shifts])
+    infos = (SolveInfo * ns)()
+    st = _lib.stag_multishift_cg(h.ptr, ptrs, _ptr(b, "b", n), float(mass), sh, ns, ctypes.byref(p), infos, _stream(stream))
+    if raise_on_error and st != STAG_OK:
+        raise StagError(st, "stag_multishift_cg")
+    out = [i.as_dict() for i in infos]
+    for d in out:
+        d["return"] = st
+    return out
+
+
+def stag_strerror(status):
+    return strerror(status)
+
+
+def stag_profile_enable(on=True):
+    _check(_lib.stag_profile_enable(1 if on else 0), "stag_profile_enable")
+
+
+def stag_profile_reset():
+    _check(_lib.stag_profile_reset(), "stag_profile_reset")
+
+
+def stag_profile_read(family):
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    _check(_lib.stag_profile_read(family.encode(), ctypes.byref(n), ctypes.byref(ms)), "stag_profile_read")
+    return n.value, ms.value
+
+
+def stag_launch_count():
+    return int(_lib.stag_launch_count())

@@ -1,0 +1,510 @@
+// common.cuh -- shared device definitions of libstag: lattice geometry on a
+// checkerboard, complex helpers, storage precisions, deterministic FP64 grid
+// reductions and the solver scalar state they finalise.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stag {
+
+// ------------------------------------------------------------------ geometry
+// Checkerboard (single-parity) index s of a site = lex/2, lex = x + Lx*(y +
+// Ly*(z + Lz*t)).  With Lx even, s = x/2 + Lxh*(y + Ly*(z + Lz*t)), so a
+// step along y, z, t moves s by a fixed stride and x is rebuilt from the
+// parity of the site.
+struct Geom {
+  int L[4];  // Lx, Ly, Lz, Lt (even, >= 4)
+  int Lxh;   // Lx / 2
+  int Vh;    // sites per parity
+  int sy, sz, st;  // checkerboard strides of y, z, t
+};
+
+struct Coord {
+  int x, y, z, t;
+};
+
+__host__ __device__ inline Geom make_geom(const int d[4]) {
+  Geom g;
+  for (int i = 0; i < 4; ++i) g.L[i] = d[i];
+  g.Lxh = d[0] / 2;
+  g.sy = g.Lxh;
+  g.sz = g.Lxh * d[1];
+  g.st = g.Lxh * d[1] * d[2];
+  g.Vh = g.st * d[3];
+  return g;
+}
+
+__device__ __forceinline__ Coord cb_coords(const Geom& g, int s, int parity) {
+  int xh = s % g.Lxh;
+  int r = s / g.Lxh;
+  Coord c;
+  c.y = r % g.L[1];
+  r /= g.L[1];
+  c.z = r % g.L[2];
+  c.t = r / g.L[2];
+  c.x = 2 * xh + ((parity + c.y + c.z + c.t) & 1);
+  return c;
+}
+
+__device__ __forceinline__ int wrapc(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
+
+// Checkerboard index of the site c + k*mu (k in {-3,-1,1,3}); s is c's own index.
+__device__ __forceinline__ int cb_neighbour(const Geom& g, int s, const Coord& c, int mu, int k) {
+  switch (mu) {
+    case 0: return s - (c.x >> 1) + (wrapc(c.x + k, g.L[0]) >> 1);
+    case 1: return s + (wrapc(c.y + k, g.L[1]) - c.y) * g.sy;
+    case 2: return s + (wrapc(c.z + k, g.L[2]) - c.z) * g.sz;
+    default: return s + (wrapc(c.t + k, g.L[3]) - c.t) * g.st;
+  }
+}
+
+// Staggered phase eta_mu(x) as a sign bit: 1 means -1.
+__device__ __forceinline__ int eta_bit(const Coord& c, int mu) {
+  int e = (mu == 0) ? 0 : (mu == 1) ? c.x : (mu == 2) ? c.x + c.y : c.x + c.y + c.z;
+  return e & 1;
+}
+
+// ------------------------------------------------------------------ complex
+template <class R> struct C2;
+template <> struct C2<double> { using T = double2; };
+template <> struct C2<float> { using T = float2; };
+
+template <class T2> __device__ __forceinline__ T2 mk(decltype(T2::x) a, decltype(T2::x) b) {
+  T2 r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+
+// acc += a * b
+template <class T2> __device__ __forceinline__ void cmac(T2& acc, T2 a, T2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <class T2> __device__ __forceinline__ void cmac_conj(T2& acc, T2 a, T2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+// ------------------------------------------------------------------ precision
+// Storage formats, by tag P:
+//   64: FP64 (double2 per complex)          32: FP32 (float2)
+//   16: IEEE binary16 (__half2)             15: 16-bit fixed point (short2,
+//       15 fraction bits), values in units of a per-site or per-field scale.
+// Arithmetic is FP64 for P = 64 and FP32 otherwise.
+template <int P> struct Prec;
+template <> struct Prec<64> {
+  using S2 = double2;
+  using A = double;
+  using A2 = double2;
+};
+template <> struct Prec<32> {
+  using S2 = float2;
+  using A = float;
+  using A2 = float2;
+};
+template <> struct Prec<16> {
+  using S2 = __half2;
+  using A = float;
+  using A2 = float2;
+};
+template <> struct Prec<15> {
+  using S2 = short2;
+  using A = float;
+  using A2 = float2;
+};
+
+constexpr float FX_ONE = 32767.0f;  // fixed-point full scale
+
+// ---- 16-byte link chunks: complex numbers packed PER to a 16-byte word so
+// that every link load is a 128-bit load.  get() returns the stored value as
+// a normalised number (for the 16-bit formats: in [-1, 1], to be multiplied
+// by the field's scale).
+template <int P> struct Chunk;
+template <> struct Chunk<64> {
+  static constexpr int PER = 1;
+  static __device__ __forceinline__ double2 get(const uint4& c, int) {
+    return make_double2(__hiloint2double(c.y, c.x), __hiloint2double(c.w, c.z));
+  }
+};
+template <> struct Chunk<32> {
+  static constexpr int PER = 2;
+  static __device__ __forceinline__ float2 get(const uint4& c, int lane) {
+    return lane == 0 ? make_float2(__uint_as_float(c.x), __uint_as_float(c.y))
+                     : make_float2(__uint_as_float(c.z), __uint_as_float(c.w));
+  }
+};
+__device__ __forceinline__ unsigned word_of(const uint4& c, int lane) {
+  return lane == 0 ? c.x : lane == 1 ? c.y : lane == 2 ? c.z : c.w;
+}
+__device__ __forceinline__ float2 half2_bits_to_float2(unsigned w) {
+  __half2_raw r;
+  r.x = (unsigned short)(w & 0xffffu);
+  r.y = (unsigned short)(w >> 16);
+  return __half22float2(__half2(r));
+}
+__device__ __forceinline__ float2 short2_bits_to_float2(unsigned w) {
+  return make_float2((float)(short)(w & 0xffffu), (float)(short)(w >> 16));
+}
+template <> struct Chunk<16> {
+  static constexpr int PER = 4;
+  static __device__ __forceinline__ float2 get(const uint4& c, int lane) {
+    return half2_bits_to_float2(word_of(c, lane));
+  }
+};
+template <> struct Chunk<15> {
+  static constexpr int PER = 4;
+  static __device__ __forceinline__ float2 get(const uint4& c, int lane) {
+    float2 v = short2_bits_to_float2(word_of(c, lane));
+    return make_float2(v.x * (1.0f / FX_ONE), v.y * (1.0f / FX_ONE));
+  }
+};
+
+// A single-parity colour-vector field in the internal layout:
+//   P = 64: [Vh][3] double2 (array of structures, the canonical layout)
+//   P = 32: [3][Vh] float2  (structure of arrays)
+//   P = 16, 15: [Vh] 16-byte records {c0, c1, c2, scale}: three complex in
+//           16-bit storage and one FP32 per-site scale, so that a
+//           neighbour gather is a single 128-bit load.
+// ld() uses the read-only path (fields not written by the same kernel),
+// ldw() plain loads (fields the kernel also writes).
+template <int P> struct Spinor {
+  void* v;
+  int Vh;
+};
+
+template <int P> __host__ __device__ inline size_t spinor_bytes(int Vh) {
+  return P == 64 ? (size_t)Vh * 48 : P == 32 ? (size_t)Vh * 24 : (size_t)Vh * 16;
+}
+
+template <int P> struct SpinorLoad;
+template <> struct SpinorLoad<64> {
+  static __device__ __forceinline__ void ld(const Spinor<64>& f, int s, double2 o[3]) {
+    const double2* p = (const double2*)f.v + 3 * (size_t)s;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[c] = __ldg(p + c);
+  }
+  static __device__ __forceinline__ void ldw(const Spinor<64>& f, int s, double2 o[3]) {
+    const double2* p = (const double2*)f.v + 3 * (size_t)s;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[c] = p[c];
+  }
+  static __device__ __forceinline__ void st(const Spinor<64>& f, int s, const double2 o[3]) {
+    double2* p = (double2*)f.v + 3 * (size_t)s;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[c] = o[c];
+  }
+};
+template <> struct SpinorLoad<32> {
+  static __device__ __forceinline__ void ld(const Spinor<32>& f, int s, float2 o[3]) {
+    const float2* p = (const float2*)f.v;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[c] = __ldg(p + c * (size_t)f.Vh + s);
+  }
+  static __device__ __forceinline__ void ldw(const Spinor<32>& f, int s, float2 o[3]) {
+    const float2* p = (const float2*)f.v;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[c] = p[c * (size_t)f.Vh + s];
+  }
+  static __device__ __forceinline__ void st(const Spinor<32>& f, int s, const float2 o[3]) {
+    float2* p = (float2*)f.v;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[c * (size_t)f.Vh + s] = o[c];
+  }
+};
+
+// 16-bit records.  FP16: components stored as value/max (round to nearest
+// even), scale = max.  Fixed point: components stored as round(value/max *
+// 32767), scale = max/32767.  max = largest |re|, |im| of the site.
+template <int P> struct SpinorLoad16 {
+  static __device__ __forceinline__ void unpack(const uint4& r, float2 o[3]) {
+    const float k = __uint_as_float(r.w);
+    float2 a = P == 16 ? half2_bits_to_float2(r.x) : short2_bits_to_float2(r.x);
+    float2 b = P == 16 ? half2_bits_to_float2(r.y) : short2_bits_to_float2(r.y);
+    float2 c = P == 16 ? half2_bits_to_float2(r.z) : short2_bits_to_float2(r.z);
+    o[0] = make_float2(a.x * k, a.y * k);
+    o[1] = make_float2(b.x * k, b.y * k);
+    o[2] = make_float2(c.x * k, c.y * k);
+  }
+  static __device__ __forceinline__ void ld(const Spinor<P>& f, int s, float2 o[3]) {
+    unpack(__ldg((const uint4*)f.v + s), o);
+  }
+  static __device__ __forceinline__ void ldw(const Spinor<P>& f, int s, float2 o[3]) {
+    unpack(((const uint4*)f.v)[s], o);
+  }
+  static __device__ __forceinline__ unsigned pack2(float x, float y) {
+    if (P == 16) {
+      __half2_raw r = (__half2_raw)__floats2half2_rn(x, y);
+      return (unsigned)r.x | ((unsigned)r.y << 16);
+    } else {
+      int a = __float2int_rn(x), b = __float2int_rn(y);
+      a = max(-32767, min(32767, a));
+      b = max(-32767, min(32767, b));
+      return (unsigned)(unsigned short)(short)a | ((unsigned)(unsigned short)(short)b << 16);
+    }
+  }
+  static __device__ __forceinline__ void st(const Spinor<P>& f, int s, const float2 o[3]) {
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m = fmaxf(m, fmaxf(fabsf(o[c].x), fabsf(o[c].y)));
+    const float full = P == 16 ? 1.0f : FX_ONE;
+    const float inv = m > 0.f ? full / m : 0.f;
+    uint4 r;
+    r.x = pack2(o[0].x * inv, o[0].y * inv);
+    r.y = pack2(o[1].x * inv, o[1].y * inv);
+    r.z = pack2(o[2].x * inv, o[2].y * inv);
+    r.w = __float_as_uint(m / full);
+    ((uint4*)f.v)[s] = r;
+  }
+};
+template <> struct SpinorLoad<16> : SpinorLoad16<16> {};
+template <> struct SpinorLoad<15> : SpinorLoad16<15> {};
+
+// ------------------------------------------------------------------ solver state
+enum StateFlags : int {
+  F_CONVERGED = 1,  // iterated residual reached the target
+  F_BREAKDOWN = 2,  // NaN/Inf or <p,Ap> <= 0
+  F_NEED_RU = 4,    // reliable-update trigger
+  F_ITER_CAP = 8,   // max_iter reached
+  F_STOP = F_CONVERGED | F_BREAKDOWN | F_ITER_CAP,
+};
+
+// Scalars of one CG solve, resident in device memory and updated by the
+// last block of each reduction (no host round trip per iteration).
+struct CgState {
+  double rr;       // iterated ||r||^2
+  double rr_prev;  // ||r||^2 of the previous iteration
+  double pAp, alpha, beta;
+  double target;   // tol^2 ||b||^2
+  double rr_max;   // max ||r||^2 since the last reliable update
+  double delta2;   // delta^2; 0 disables the reliable-update trigger
+  double rr_true;  // last FP64 true ||r||^2
+  double ortho_re, ortho_im;  // <r,p>/||r||^2 used to re-orthogonalise p
+  double shift;    // m^2 + sigma of this system
+  int iter, max_iter;
+  int flags;
+  int reliable_updates;
+};
+
+constexpr int MAX_SHIFTS = 32;
+// Scalars of a multi-shift solve: the base system's CG scalars plus the
+// per-shift zeta / alpha / beta recurrences.
+struct MsState {
+  CgState cg;       // base system (smallest shift)
+  int nshift;
+  int active_mask;  // bit s set while shift s still iterates
+  int stop_mask;    // shifts that reached their target in the last iteration
+  double sqrt_target_bb;  // tol * ||b||
+  double alpha_prev, beta_prev;
+  double delta[MAX_SHIFTS];      // sigma_s - sigma_0
+  double zeta_prev[MAX_SHIFTS];  // zeta_s(k-1)
+  double zeta[MAX_SHIFTS];       // zeta_s(k)
+  double zeta_next[MAX_SHIFTS];  // zeta_s(k+1)
+  double alpha_s[MAX_SHIFTS];
+  double beta_s[MAX_SHIFTS];
+  int iters[MAX_SHIFTS];
+};
+
+enum RedOp : int {
+  RED_STORE = 0,      // out[0..NV) = totals
+  RED_CG_ALPHA = 1,   // pAp -> alpha
+  RED_CG_BETA = 2,    // ||r||^2 -> beta, flags
+  RED_RU_RESID = 3,   // true ||r||^2 after a reliable update
+  RED_RU_ORTHO = 4,   // <r,p> (re, im) -> ortho coefficient
+  RED_MS_ALPHA = 5,   // base pAp -> alpha and per-shift zeta, alpha_s
+  RED_MS_BETA = 6,    // ||r||^2 -> beta, per-shift beta_s, shift stopping
+};
+
+struct RedTarget {
+  int op;
+  void* state;   // CgState* or MsState*
+  double* out;   // RED_STORE destination
+};
+
+struct RedBuf {
+  double* partials;   // [NV][gridDim.x]
+  unsigned* counter;  // zero between reductions
+};
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+__device__ inline void cg_beta_update(CgState* st, double rr_new) {
+  if (!finite_d(rr_new)) {
+    st->flags |= F_BREAKDOWN;
+    return;
+  }
+  st->beta = rr_new / st->rr;
+  st->rr_prev = st->rr;
+  st->rr = rr_new;
+  st->iter += 1;
+  if (rr_new > st->rr_max) st->rr_max = rr_new;
+  if (rr_new <= st->target) st->flags |= F_CONVERGED;
+  if (st->delta2 > 0.0 && rr_new < st->delta2 * st->rr_max) st->flags |= F_NEED_RU;
+  if (st->iter >= st->max_iter) st->flags |= F_ITER_CAP;
+}
+
+__device__ inline void finalize(const RedTarget& t, const double* v, int nv) {
+  switch (t.op) {
+    case RED_STORE:
+      for (int i = 0; i < nv; ++i) t.out[i] = v[i];
+      break;
+    case RED_CG_ALPHA: {
+      CgState* st = (CgState*)t.state;
+      st->pAp = v[0];
+      if (!(v[0] > 0.0) || !finite_d(v[0])) st->flags |= F_BREAKDOWN;
+      else st->alpha = st->rr / v[0];
+      break;
+    }
+    case RED_CG_BETA:
+      cg_beta_update((CgState*)t.state, v[0]);
+      break;
+    case RED_RU_RESID: {
+      CgState* st = (CgState*)t.state;
+      double rr = v[0];
+      st->rr_true = rr;
+      if (!finite_d(rr)) {
+        st->flags |= F_BREAKDOWN;
+        break;
+      }
+      st->beta = rr / st->rr_prev;
+      st->rr = rr;
+      st->rr_max = rr;
+      st->reliable_updates += 1;
+      st->flags &= ~(F_CONVERGED | F_NEED_RU);
+      break;
+    }
+    case RED_RU_ORTHO: {
+      CgState* st = (CgState*)t.state;
+      st->ortho_re = st->rr > 0.0 ? v[0] / st->rr : 0.0;
+      st->ortho_im = st->rr > 0.0 ? v[1] / st->rr : 0.0;
+      break;
+    }
+    case RED_MS_ALPHA: {
+      MsState* ms = (MsState*)t.state;
+      CgState* st = &ms->cg;
+      st->pAp = v[0];
+      if (!(v[0] > 0.0) || !finite_d(v[0])) {
+        st->flags |= F_BREAKDOWN;
+        break;
+      }
+      double a = st->rr / v[0];
+      st->alpha = a;
+      // the previous iteration's shift update has consumed zeta(k+1): rotate,
+      // and retire the shifts that reached their target
+      for (int s = 0; s < ms->nshift; ++s) {
+        ms->zeta_prev[s] = ms->zeta[s];
+        ms->zeta[s] = ms->zeta_next[s];
+      }
+      ms->active_mask &= ~ms->stop_mask;
+      ms->stop_mask = 0;
+      for (int s = 0; s < ms->nshift; ++s) {
+        if (!((ms->active_mask >> s) & 1)) continue;
+        double zp = ms->zeta_prev[s], z = ms->zeta[s];
+        double den = ms->alpha_prev * zp * (1.0 + a * ms->delta[s]) + a * ms->beta_prev * (zp - z);
+        double zn = z * zp * ms->alpha_prev / den;
+        ms->zeta_next[s] = zn;
+        ms->alpha_s[s] = a * zn / z;
+      }
+      break;
+    }
+    case RED_MS_BETA: {
+      MsState* ms = (MsState*)t.state;
+      CgState* st = &ms->cg;
+      double rr_new = v[0];
+      if (!finite_d(rr_new)) {
+        st->flags |= F_BREAKDOWN;
+        break;
+      }
+      double b = rr_new / st->rr;
+      st->beta = b;
+      st->rr_prev = st->rr;
+      st->rr = rr_new;
+      st->iter += 1;
+      double rn = sqrt(rr_new);
+      int mask = ms->active_mask;
+      for (int s = 0; s < ms->nshift; ++s) {
+        if (!((mask >> s) & 1)) continue;
+        double ratio = ms->zeta_next[s] / ms->zeta[s];
+        ms->beta_s[s] = b * ratio * ratio;
+        ms->iters[s] = st->iter;
+      }
+      ms->alpha_prev = st->alpha;
+      ms->beta_prev = b;
+      // shifts whose residual |zeta_s| ||r|| reached the target still take
+      // this iteration's update; they are retired at the next alpha step
+      int stop = 0;
+      for (int s = 0; s < ms->nshift; ++s)
+        if (((mask >> s) & 1) && fabs(ms->zeta_next[s]) * rn <= ms->sqrt_target_bb) stop |= 1 << s;
+      ms->stop_mask = stop;
+      if ((mask & ~stop) == 0) st->flags |= F_CONVERGED;
+      if (st->iter >= st->max_iter) st->flags |= F_ITER_CAP;
+      break;
+    }
+  }
+}
+
+// Deterministic block sum of NV doubles; the total is valid in thread 0.
+template <int NV> __device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sm[NV][32];
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sm[i][w] = v[i];
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  if (w == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      v[i] = (l < nw) ? sm[i][l] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+  }
+  __syncthreads();
+}
+
+// Grid-wide sum: each block stores its partial, the last block to finish
+// (atomic ticket) adds the partials in block order and finalises.  Every
+// thread of every block must call this (no early return before it).
+template <int NV> __device__ __forceinline__ void grid_reduce(double (&v)[NV], RedBuf rb, RedTarget tgt) {
+  block_sum<NV>(v);
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) rb.partials[i * gridDim.x + blockIdx.x] = v[i];
+    __threadfence();
+    unsigned t = atomicAdd(rb.counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double w[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) w[i] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) w[i] += __ldcg(rb.partials + i * gridDim.x + b);
+  block_sum<NV>(w);
+  if (threadIdx.x == 0) {
+    finalize(tgt, w, NV);
+    *rb.counter = 0u;
+    __threadfence();
+  }
+}
+
+// Early-exit test shared by the Krylov-loop kernels.
+__device__ __forceinline__ bool stopped(const int* flags) { return flags != nullptr && (__ldcg(flags) & F_STOP); }
+
+}  // namespace stag

@@ -1,0 +1,140 @@
+// internal.h -- host-side internals of libstag shared by its translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+
+#include "../../include/stag.h"
+#include "common.cuh"
+
+namespace stag {
+
+// One precision copy of the gauge field in the internal layout (see
+// links.cu): per output parity, the 16 hop matrices of every site with the
+// staggered phase, the 1/2 and the backward sign folded in, packed into
+// 16-byte chunks stored [chunk][site].  With NL = 6 only rows 0, 1 of the
+// SU(3) part of each Naik hop are kept and the factor +-1/2 eta c3 is applied
+// in-kernel.
+struct LinkCopy {
+  bool present = false;
+  void* data = nullptr;     // [2 parities][chunks][Vh] 16-byte chunks
+  size_t parity_stride = 0; // bytes per parity
+  int nl = 9;
+  float fat_scale = 1.f;    // 16-bit formats: stored (normalised) value * scale
+  float long_scale = 1.f;   //   = matrix entry
+  size_t elem_bytes = 0;    // bytes of one stored complex
+};
+
+struct Workspace {
+  std::map<std::string, std::pair<void*, size_t>> bufs;
+  ~Workspace();
+  // Device buffer of at least `bytes` bytes under `name` (contents kept only
+  // while the size does not grow; *fresh set when newly allocated).
+  void* get(const std::string& name, size_t bytes, int* status, bool* fresh = nullptr);
+  void release();
+};
+
+}  // namespace stag
+
+struct stag_lattice_s {
+  stag::Geom g;
+  int dims[4];
+  double c3 = -1.0 / 24.0;
+  stag::LinkCopy links[4];  // by stag_prec
+  stag::Workspace ws;
+};
+
+namespace stag {
+
+// ------------------------------------------------------------ instrumentation
+void prof_begin(const char* family, cudaStream_t s);
+void prof_end(cudaStream_t s);
+void prof_flush_completed();
+void count_launch();
+
+struct ProfScope {
+  cudaStream_t s;
+  ProfScope(const char* family, cudaStream_t st) : s(st) {
+    count_launch();
+    prof_begin(family, st);
+  }
+  ~ProfScope() { prof_end(s); }
+};
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? STAG_OK : STAG_ECUDA; }
+int last_launch_status();
+
+// Reduction scratch: [2][max_grid] partial sums and a ticket counter.
+struct RedScratch {
+  double* partials;
+  unsigned* counter;
+  int max_grid;
+};
+int get_red_scratch(stag_lattice_s* lat, const char* name, RedScratch* out);
+
+// A Spinor<P> living in the handle's workspace buffer `name`.
+template <int P> Spinor<P> ws_spinor(stag_lattice_s* lat, const std::string& name, int* status);
+
+// ------------------------------------------------------------------- links
+int build_link_copy(stag_lattice_s* lat, int prec, int recon, const double2* fat, const double2* lng,
+                    cudaStream_t st);
+
+// ------------------------------------------------------------------- dslash
+// Storage format P of the links and spinors (64, 32, 16 = binary16, 15 =
+// 16-bit fixed point); accumulation precision PA = 64 for P = 64, else 32.
+template <int P> struct Acc { static constexpr int value = (P == 64) ? 64 : 32; };
+template <int P> constexpr int prec_index() {
+  return P == 64 ? STAG_FP64 : P == 32 ? STAG_FP32 : P == 16 ? STAG_FP16 : STAG_FX16;
+}
+
+template <int P>
+int launch_dslash(const stag_lattice_s* lat, Spinor<P> out, Spinor<P> in, int out_parity, const int* flags,
+                  cudaStream_t st);
+
+// out = ax * x + ay * y + ad * (D in) on parity out_parity, and optionally a
+// reduction: red = 1: Re <x, out>; red = 2: ||out||^2.
+template <int P>
+int launch_dslash_epi(const stag_lattice_s* lat, Spinor<Acc<P>::value> out, Spinor<P> in, int out_parity,
+                      Spinor<P> x, double ax, Spinor<Acc<P>::value> y, double ay, double ad, int red,
+                      RedScratch rs, RedTarget tgt, const int* flags, cudaStream_t st);
+
+// ------------------------------------------------------------------- blas
+// canonical [Vh][3] complex double <-> internal Spinor<P>
+template <int P> int launch_from_canonical(Spinor<P> out, const double2* in, int Vh, cudaStream_t st);
+template <int P> int launch_to_canonical(double2* out, Spinor<P> in, int Vh, cudaStream_t st);
+// out (precision PO) = in (precision PI)
+template <int PO, int PI> int launch_convert(Spinor<PO> out, Spinor<PI> in, cudaStream_t st);
+int launch_zero(void* p, size_t bytes, cudaStream_t st);
+
+// ||v||^2 (FP64) or Re<a,b>, Im<a,b> into a RedTarget.
+template <int P> int launch_norm2(Spinor<P> v, RedScratch rs, RedTarget tgt, cudaStream_t st);
+
+// CG update: xh += alpha p; rh -= alpha Ap; ||rh||^2 -> RED_CG_BETA.
+template <int P>
+int launch_cg_update(Spinor<Acc<P>::value> xh, Spinor<Acc<P>::value> rh, Spinor<P> p, Spinor<Acc<P>::value> Ap,
+                     CgState* state, RedScratch rs, cudaStream_t st);
+// p = rh + beta p
+template <int P> int launch_cg_xpay(Spinor<P> p, Spinor<Acc<P>::value> rh, CgState* state, cudaStream_t st);
+// y += xh; xh = 0   (y FP64)
+template <int PV> int launch_accumulate(Spinor<64> y, Spinor<PV> xh, cudaStream_t st);
+// rh = convert(r64) and <rh, p> -> RED_RU_ORTHO
+template <int P>
+int launch_ru_convert_dot(Spinor<Acc<P>::value> rh, Spinor<64> r, Spinor<P> p, CgState* state, RedScratch rs,
+                          cudaStream_t st);
+// p = rh + beta (p - ortho rh)
+template <int P> int launch_ru_p(Spinor<P> p, Spinor<Acc<P>::value> rh, CgState* state, cudaStream_t st);
+
+// Multi-shift: r -= alpha Ap; ||r||^2 -> RED_MS_BETA
+template <int P>
+int launch_ms_r_update(Spinor<Acc<P>::value> r, Spinor<Acc<P>::value> Ap, MsState* state, RedScratch rs,
+                       cudaStream_t st);
+// for every active shift s: x_s += alpha_s p_s; p_s = zeta_s r + beta_s p_s
+// Runs only when the state's iteration count equals expect_iter (the residual
+// update of this iteration ran); `base` is the smallest shift.
+template <int P>
+int launch_ms_shift_update(Spinor<64>* xs, Spinor<P>* ps, int nshift, int base, Spinor<Acc<P>::value> r,
+                           MsState* state, int expect_iter, cudaStream_t st);
+
+}  // namespace stag

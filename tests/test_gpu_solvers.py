@@ -1,0 +1,141 @@
+"""GPU solver parity: every solve must reach 1e-10 relative true residual,
+recomputed independently by the FP64 oracle on the host; the distance to the
+oracle's own solution is reported and bounded by a condition-number margin
+(solutions at 1e-10 residual may differ by up to ~kappa * 1e-10)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_common import Field, dev, rel_l2, requires_gpu
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+
+def _stag():
+    import paper_1712_00143_gb300 as stag
+
+    return stag
+
+
+@pytest.mark.parametrize("mode", ["plain64", "mixed32", "mixed16", "mixedfx16"])
+@pytest.mark.parametrize("recon", [18, 12])
+def test_cg_8_4(mode, recon):
+    """8^4, m = 0.1, Gaussian even source: the small single-mass workload."""
+    stag = _stag()
+    dims = (8, 8, 8, 8)
+    f = Field.get(dims)
+    h = f.handle(recon=recon)
+    b = synth.gaussian_source(dims, 5000)
+    x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    info = stag.stag_cg(h, x, dev(b), 0.1, mode=mode, tol=1e-10)
+    xs = x.cpu().numpy()
+    res = oracle.true_residual(f.fat, f.lng, xs, b, 0.1, dims)
+    xo, oi = oracle.cg(f.fat, f.lng, b, 0.1, dims, tol=1e-12)
+    assert info["converged"] == 1 and info["status"] == 0
+    assert res <= 1e-10, res
+    assert abs(info["true_rel_resid"] - res) < 1e-12
+    assert rel_l2(xs, xo) < 1e-7
+    if mode != "plain64":
+        assert info["reliable_updates"] >= 2
+    h.free()
+
+
+def test_cg_ragged_lattice_initial_guess():
+    stag = _stag()
+    dims = (4, 6, 8, 10)
+    f = Field.get(dims)
+    h = f.handle(recon=12)
+    b = synth.gaussian_source(dims, 5001)
+    xo, _ = oracle.cg(f.fat, f.lng, b, 0.05, dims, tol=1e-12)
+    x0 = xo + 1e-4 * synth.random_spinor(dims, 3)
+    x = dev(x0)
+    info = stag.stag_cg(h, x, dev(b), 0.05, mode="mixed32", use_initial_guess=1)
+    res = oracle.true_residual(f.fat, f.lng, x.cpu().numpy(), b, 0.05, dims)
+    assert info["converged"] and res <= 1e-10
+    h.free()
+
+
+def test_cg_32_4_mixed_headline_workload():
+    """32^4, m = 0.01: the headline solve, mixed 16-bit fixed point and FP32, recon-12."""
+    stag = _stag()
+    dims = (32, 32, 32, 32)
+    f = Field.get(dims)
+    h = f.handle(recon=12)
+    b = synth.gaussian_source(dims, 5000)
+    bd = dev(b)
+    for mode in ("mixedfx16", "mixed32"):
+        x = torch.zeros_like(bd)
+        info = stag.stag_cg(h, x, bd, 0.01, mode=mode, tol=1e-10)
+        res = oracle.true_residual(f.fat, f.lng, x.cpu().numpy(), b, 0.01, dims)
+        assert info["converged"] and res <= 1e-10, (mode, info, res)
+    h.free()
+
+
+def test_multishift_8_4():
+    stag = _stag()
+    dims = (8, 8, 8, 8)
+    f = Field.get(dims)
+    h = f.handle(recon=12)
+    b = synth.gaussian_source(dims, 5002)
+    shifts = [10 ** (-4 + k / 2) for k in range(9)]
+    for mode in ("plain64", "mixed32", "mixed16", "mixedfx16"):
+        xs = [torch.zeros(b.shape, dtype=torch.complex128, device="cuda") for _ in shifts]
+        infos = stag.stag_multishift_cg(h, xs, dev(b), 0.05, shifts, mode=mode, tol=1e-10)
+        for s, x, inf in zip(shifts, xs, infos):
+            res = oracle.true_residual(f.fat, f.lng, x.cpu().numpy(), b, 0.05, dims, shift=s)
+            assert inf["converged"] and res <= 1e-10, (mode, s, inf, res)
+        if mode == "plain64":
+            # shared Krylov space: the larger shifts stop earlier
+            its = [inf["iters"] for inf in infos]
+            assert its == sorted(its, reverse=True)
+    h.free()
+
+
+def test_multishift_matches_oracle_multishift():
+    stag = _stag()
+    dims = (4, 6, 8, 10)
+    f = Field.get(dims)
+    h = f.handle()
+    b = synth.gaussian_source(dims, 5003)
+    shifts = [0.3, 0.0, 0.02]
+    xo, _ = oracle.multishift_cg(f.fat, f.lng, b, 0.1, shifts, dims, tol=1e-12)
+    xs = [torch.zeros(b.shape, dtype=torch.complex128, device="cuda") for _ in shifts]
+    stag.stag_multishift_cg(h, xs, dev(b), 0.1, shifts, mode="plain64", tol=1e-12)
+    for x, r in zip(xs, xo):
+        assert rel_l2(x.cpu().numpy(), r) < 1e-9
+    h.free()
+
+
+def test_not_converged_status():
+    stag = _stag()
+    dims = (8, 8, 8, 8)
+    f = Field.get(dims)
+    h = f.handle()
+    b = synth.gaussian_source(dims, 5000)
+    x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    info = stag.stag_cg(h, x, dev(b), 0.1, mode="mixed32", max_iter=5, check_interval=2, raise_on_error=False)
+    assert info["return"] == stag.STAG_ENOTCONV and not info["converged"]
+    assert 5 <= info["iters"] <= 6
+    # x holds the last iterate: its residual is below the starting one
+    res = oracle.true_residual(f.fat, f.lng, x.cpu().numpy(), b, 0.1, dims)
+    assert res < 1.0 and abs(res - info["true_rel_resid"]) < 1e-12
+    h.free()
+
+
+def test_zero_source_and_non_unitary_links():
+    stag = _stag()
+    dims = (4, 4, 4, 4)
+    f = Field.get(dims)
+    h = f.handle()
+    b = torch.zeros((h.Vh, 3), dtype=torch.complex128, device="cuda")
+    x = torch.ones_like(b)
+    info = stag.stag_cg(h, x, b, 0.1)
+    assert info["converged"] and float(x.abs().max()) == 0.0
+    h.free()
+    # fat links are not c3 * SU(3): recon-12 must refuse them
+    with pytest.raises(stag.StagError) as e:
+        stag.stag_load_links(dims, f.fat_d, f.fat_d, recon_long=12)
+    assert e.value.status == stag.STAG_ENOTUNITARY
