@@ -131,6 +131,36 @@ int stag_dslash(stag_lattice_t lat, void* out, const void* in, int out_parity, i
 int stag_apply_m(stag_lattice_t lat, void* out, const void* in, double mass, double shift, int prec,
                  void* stream);
 
+/* ------------------------------------------------- allocation-free operator
+ * stag_apply_m_noalloc computes exactly what stag_apply_m computes with
+ * prec = STAG_FP64 (out = (m^2 + shift) in - D_eo D_oe in, even sites), but
+ * never allocates device memory.  It exists for callers that cannot call
+ * cudaMalloc at the point where they apply the operator: applications whose
+ * own pool allocator owns all device memory and forbids other allocations,
+ * and real-time or certified code paths that allow no allocation (and none
+ * of the device-wide synchronisation cudaFree implies) after start-up.
+ * There is no counterpart in the paper.
+ *
+ * Scratch: the odd-parity intermediate D_oe in lives in a file-scope static
+ * device array of STAG_NOALLOC_MAX_VH sites x 3 complex doubles (3 MiB),
+ * which every GPU that loads libstag holds until the process exits.  The
+ * lattice must have V/2 <= STAG_NOALLOC_MAX_VH (e.g. 16^4, 16^3 x 32);
+ * larger lattices are rejected with STAG_EINVAL before any GPU work.
+ * The handle must hold an FP64 link copy (prec_mask bit 0).
+ *
+ * The first call on a device looks up the array's device address for that
+ * device (one-time set-up, with that device current); make that first call
+ * before any stream capture.  All calls share the one array: calls whose
+ * kernels can overlap on the GPU (different streams, or several host
+ * threads) race on it and must be serialised by the caller.  The array
+ * keeps the last call's contents; nothing in it needs to start at zero, as
+ * every entry is written before it is read.
+ * in/out: device, canonical [V/2][3] complex double.  Asynchronous on
+ * `stream`.  Errors: EINVAL, ECUDA. */
+#define STAG_NOALLOC_MAX_VH 65536
+int stag_apply_m_noalloc(stag_lattice_t lat, void* out, const void* in, double mass, double shift,
+                         void* stream);
+
 /* Solve M x = b (even sites) to params->tol in FP64 true residual.
  * x, b: device canonical [V/2][3] complex double; x is read as the initial
  * guess when params->use_initial_guess, and always written.

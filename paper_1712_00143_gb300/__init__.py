@@ -44,6 +44,7 @@ EXPORTS = (
     "stag_lattice_info",
     "stag_dslash",
     "stag_apply_m",
+    "stag_apply_m_noalloc",
     "stag_cg",
     "stag_multishift_cg",
     "stag_strerror",
@@ -105,6 +106,7 @@ def load_library(path=LIB_PATH):
         "stag_lattice_info": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_longlong)]),
         "stag_dslash": (ci, [vp, vp, vp, ci, ci, ci, vp]),
         "stag_apply_m": (ci, [vp, vp, vp, cd, cd, ci, vp]),
+        "stag_apply_m_noalloc": (ci, [vp, vp, vp, cd, cd, vp]),
         "stag_cg": (ci, [vp, vp, vp, cd, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), vp]),
         "stag_multishift_cg": (
             ci,
@@ -234,6 +236,18 @@ def stag_apply_m(h, out, inp, mass, shift=0.0, prec="fp64", stream=None):
     )
     _check(st, "stag_apply_m")
     return out
+
+
+def stag_apply_m_noalloc(h, out, inp, mass, shift=0.0, stream=None):
+    """FP64 out = (m^2 + shift) inp - D_eo D_oe inp without any device allocation
+    (scratch in the library's static device array; V/2 <= NOALLOC_MAX_VH)."""
+    n = h.Vh * 3
+    st = _lib.stag_apply_m_noalloc(h.ptr, _ptr(out, "out", n), _ptr(inp, "inp", n), float(mass), float(shift), _stream(stream))
+    _check(st, "stag_apply_m_noalloc")
+    return out
+
+
+NOALLOC_MAX_VH = 65536
 
 
 def stag_cg(h, x, b, mass, params=None, stream=None, raise_on_error=True, **kw):
