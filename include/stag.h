@@ -72,6 +72,8 @@ typedef struct {
                         copies; needs L/long_coeff in SU(3), else ENOTUNITARY) */
   double long_coeff; /* c3 with L = c3 * (product of SU(3) links); -1/24 */
   unsigned prec_mask; /* bit (1 << stag_prec) per copy to build; 0 = all four */
+  int autotune;      /* 1: time the Dslash launch shapes of each copy on this
+                        lattice and keep the fastest (a few ms); 0: defaults */
 } stag_link_opts;
 
 typedef struct {
@@ -106,12 +108,18 @@ void stag_default_params(stag_solve_params* p);
  *   dims : host array {Lx, Ly, Lz, Lt}, even, each >= 4.
  *   fat, lng : device, canonical [V][4][3][3] complex double.  Copied; the
  *          caller may free them after the call returns.
- *   opts : may be NULL (recon 18, c3 = -1/24, all precisions).
+ *   opts : may be NULL (recon 18, c3 = -1/24, all precisions, autotune).
  * Errors: EINVAL, ENOMEM, ECUDA, ENOTUNITARY.  Synchronises `stream`. */
 int stag_load_links(stag_lattice_t* out, const int dims[4], const void* fat, const void* lng,
                     const stag_link_opts* opts, void* stream);
 
 int stag_free_lattice(stag_lattice_t lat);
+
+/* The launch shape the autotuner kept for a copy's Dslash kernel
+ * (kernel 0: plain, 1: fused epilogue with dot product): threads per block,
+ * minimum resident blocks per SM given to the compiler, and its timing in us
+ * per launch (0 when not tuned).  Any output pointer may be NULL. */
+int stag_tuned_shape(stag_lattice_t lat, int prec, int kernel, int* block, int* min_blocks, double* us);
 
 /* Lattice extents and the per-parity site count V/2 of a handle. */
 int stag_lattice_info(stag_lattice_t lat, int dims[4], long long* vh);
@@ -190,6 +198,11 @@ const char* stag_strerror(int status);
  * (ms).  stag_launch_count counts all library kernel launches since the last
  * reset, whether or not profiling is on. */
 int stag_profile_enable(int on);
+/* Restrict the event pairs to the listed families (comma-separated, e.g.
+ * "dslash,dslash_epi"; NULL or "" times every family) and to one launch in
+ * `every` of each family (every <= 1: all), which keeps the events' own cost
+ * out of the measured workload. */
+int stag_profile_select(const char* families, int every);
 int stag_profile_reset(void);
 int stag_profile_read(const char* family, long long* launches, double* total_ms);
 long long stag_launch_count(void);

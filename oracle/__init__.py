@@ -15,6 +15,9 @@ Parity status of each function (what pins it, checked by the CPU tests):
   * multishift_cg          -- dense LU solve per shift on 4^4, and single-mass
                               CG run shift by shift.
   * true_residual          -- exact definition ||b - M x|| / ||b||.
+  * apply_m_at_sites       -- equals apply_m restricted to the sampled sites
+                              (checked on small lattices), used to check
+                              full-size GPU results site by site.
 """
 
 from .staggered import (
@@ -24,6 +27,7 @@ from .staggered import (
     neighbour_lex,
     dslash,
     apply_m,
+    apply_m_at_sites,
     true_residual,
     cg,
     multishift_cg,
@@ -37,6 +41,7 @@ __all__ = [
     "neighbour_lex",
     "dslash",
     "apply_m",
+    "apply_m_at_sites",
     "true_residual",
     "cg",
     "multishift_cg",

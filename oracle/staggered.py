@@ -109,6 +109,23 @@ def apply_m(fat, lng, v, mass, dims, shift=0.0):
     return (mass * mass + shift) * v - dslash(fat, lng, t, dims, out_parity=0)
 
 
+def apply_m_at_sites(fat, lng, v, mass, dims, sites, shift=0.0):
+    """((m^2 + shift) v - D_eo D_oe v) at the even checkerboard sites `sites` only.
+
+    D_oe v is evaluated only on the odd neighbours (distance 1 and 3 in every
+    direction) of the requested sites, then D_eo on the requested sites: the
+    same definition as :func:`apply_m`, restricted to what those outputs read.
+    """
+    dims = tuple(dims)
+    sites = np.asarray(sites, dtype=np.int64)
+    c = site_coords(dims, parity_sites(dims, 0)[sites])
+    nb = [neighbour_lex(dims, c, mu, k) // 2 for mu in range(4) for k in (1, -1, 3, -3)]
+    nb = np.unique(np.concatenate(nb))
+    t = np.zeros_like(v)
+    t[nb] = dslash(fat, lng, v, dims, out_parity=1, out_sites=nb)
+    return (mass * mass + shift) * v[sites] - dslash(fat, lng, t, dims, out_parity=0, out_sites=sites)
+
+
 def _dot(a, b):
     """<a, b> = sum conj(a) b."""
     return np.vdot(a.ravel(), b.ravel())

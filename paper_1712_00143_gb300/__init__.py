@@ -42,6 +42,7 @@ EXPORTS = (
     "stag_load_links",
     "stag_free_lattice",
     "stag_lattice_info",
+    "stag_tuned_shape",
     "stag_dslash",
     "stag_apply_m",
     "stag_apply_m_noalloc",
@@ -49,6 +50,7 @@ EXPORTS = (
     "stag_multishift_cg",
     "stag_strerror",
     "stag_profile_enable",
+    "stag_profile_select",
     "stag_profile_reset",
     "stag_profile_read",
     "stag_launch_count",
@@ -62,7 +64,12 @@ class StagError(RuntimeError):
 
 
 class LinkOpts(ctypes.Structure):
-    _fields_ = [("recon_long", ctypes.c_int), ("long_coeff", ctypes.c_double), ("prec_mask", ctypes.c_uint)]
+    _fields_ = [
+        ("recon_long", ctypes.c_int),
+        ("long_coeff", ctypes.c_double),
+        ("prec_mask", ctypes.c_uint),
+        ("autotune", ctypes.c_int),
+    ]
 
 
 class SolveParams(ctypes.Structure):
@@ -104,6 +111,7 @@ def load_library(path=LIB_PATH):
         "stag_load_links": (ci, [ctypes.POINTER(vp), ctypes.POINTER(ci), vp, vp, ctypes.POINTER(LinkOpts), vp]),
         "stag_free_lattice": (ci, [vp]),
         "stag_lattice_info": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_longlong)]),
+        "stag_tuned_shape": (ci, [vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(cd)]),
         "stag_dslash": (ci, [vp, vp, vp, ci, ci, ci, vp]),
         "stag_apply_m": (ci, [vp, vp, vp, cd, cd, ci, vp]),
         "stag_apply_m_noalloc": (ci, [vp, vp, vp, cd, cd, vp]),
@@ -114,6 +122,7 @@ def load_library(path=LIB_PATH):
         ),
         "stag_strerror": (ctypes.c_char_p, [ci]),
         "stag_profile_enable": (ci, [ci]),
+        "stag_profile_select": (ci, [ctypes.c_char_p, ci]),
         "stag_profile_reset": (ci, []),
         "stag_profile_read": (ci, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(cd)]),
         "stag_launch_count": (ctypes.c_longlong, []),
@@ -193,13 +202,13 @@ class LatticeHandle:
             pass
 
 
-def stag_load_links(dims, fat, lng, recon_long=18, long_coeff=-1.0 / 24.0, prec_mask=0, stream=None):
+def stag_load_links(dims, fat, lng, recon_long=18, long_coeff=-1.0 / 24.0, prec_mask=0, autotune=True, stream=None):
     """Copy canonical fat/long links into a new lattice handle (see stag.h)."""
     dims = tuple(int(d) for d in dims)
     V = dims[0] * dims[1] * dims[2] * dims[3]
     h = ctypes.c_void_p()
     d = (ctypes.c_int * 4)(*dims)
-    o = LinkOpts(int(recon_long), float(long_coeff), int(prec_mask))
+    o = LinkOpts(int(recon_long), float(long_coeff), int(prec_mask), 1 if autotune else 0)
     st = _lib.stag_load_links(
         ctypes.byref(h), d, _ptr(fat, "fat", V * 36), _ptr(lng, "lng", V * 36), ctypes.byref(o), _stream(stream)
     )
@@ -209,6 +218,13 @@ def stag_load_links(dims, fat, lng, recon_long=18, long_coeff=-1.0 / 24.0, prec_
 
 def stag_free_lattice(h):
     h.free()
+
+
+def stag_tuned_shape(h, prec, kernel=0):
+    """(threads per block, min blocks per SM, us per launch) kept by the autotuner."""
+    b, m, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(_lib.stag_tuned_shape(h.ptr, _prec(prec), int(kernel), ctypes.byref(b), ctypes.byref(m), ctypes.byref(us)), "stag_tuned_shape")
+    return b.value, m.value, us.value
 
 
 def stag_lattice_info(h):
@@ -286,6 +302,12 @@ def stag_strerror(status):
 
 def stag_profile_enable(on=True):
     _check(_lib.stag_profile_enable(1 if on else 0), "stag_profile_enable")
+
+
+def stag_profile_select(families="", every=1):
+    """Time only the listed kernel families (comma-separated; "" = all), one
+    launch in `every` of each."""
+    _check(_lib.stag_profile_select(families.encode(), int(every)), "stag_profile_select")
 
 
 def stag_profile_reset():

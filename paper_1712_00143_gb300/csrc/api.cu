@@ -39,9 +39,16 @@ void* Workspace::get(const std::string& name, size_t bytes, int* status, bool* f
   return p;
 }
 
+void Workspace::drop(const std::string& name) {
+  auto it = bufs.find(name);
+  if (it == bufs.end()) return;
+  cudaFree(it->second.first);
+  bufs.erase(it);
+}
+
 int get_red_scratch(stag_lattice_s* lat, const char* name, RedScratch* out) {
   int st = 0;
-  int max_grid = (lat->g.Vh + 255) / 256;
+  int max_grid = (lat->g.Vh + 127) / 128;  // one block per 128 sites at most
   if (max_grid < 1024) max_grid = 1024;
   std::string n(name);
   double* p = (double*)lat->ws.get(n + ".partials", sizeof(double) * 2 * (size_t)max_grid, &st);
@@ -69,6 +76,9 @@ struct Rec {
 };
 std::mutex g_mu;
 bool g_prof = false;
+std::string g_filter;  // comma-separated families to time; empty = all
+long long g_every = 1;  // time one launch in g_every of each selected family
+std::map<std::string, long long> g_seen;
 std::atomic<long long> g_launches{0};
 std::vector<Rec> g_open;
 std::vector<cudaEvent_t> g_pool;
@@ -126,10 +136,25 @@ void flush_locked(bool wait) {
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+bool family_selected(const char* family) {
+  if (g_filter.empty()) return true;
+  const std::string f(family);
+  size_t pos = 0;
+  while (pos <= g_filter.size()) {
+    size_t end = g_filter.find(',', pos);
+    if (end == std::string::npos) end = g_filter.size();
+    if (g_filter.compare(pos, end - pos, f) == 0) return true;
+    pos = end + 1;
+  }
+  return false;
+}
+
 void prof_begin(const char* family, cudaStream_t s) {
   t_pending = -1;
   if (!g_prof) return;
   std::lock_guard<std::mutex> lk(g_mu);
+  if (!family_selected(family)) return;
+  if (g_every > 1 && (g_seen[family]++ % g_every) != 0) return;
   if (g_open.size() > 8192) flush_locked(false);
   cudaEvent_t a = take_event();
   if (!a) return;
@@ -193,6 +218,14 @@ int stag_profile_enable(int on) {
   return STAG_OK;
 }
 
+int stag_profile_select(const char* families, int every) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_filter = families ? families : "";
+  g_every = every > 1 ? every : 1;
+  g_seen.clear();
+  return STAG_OK;
+}
+
 int stag_profile_reset(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   flush_locked(true);
@@ -227,6 +260,7 @@ int stag_load_links(stag_lattice_t* out, const int dims[4], const void* fat, con
   o.recon_long = 18;
   o.long_coeff = -1.0 / 24.0;
   o.prec_mask = 0;
+  o.autotune = 1;
   if (opts) o = *opts;
   if (o.recon_long != 18 && o.recon_long != 12) return STAG_EINVAL;
   if (o.recon_long == 12 && !(o.long_coeff != 0.0)) return STAG_EINVAL;
@@ -240,6 +274,14 @@ int stag_load_links(stag_lattice_t* out, const int dims[4], const void* fat, con
   for (int p = 0; p < 4; ++p) {
     if (!((mask >> p) & 1)) continue;
     int s = build_link_copy(lat, p, o.recon_long, (const double2*)fat, (const double2*)lng, st);
+    if (!s && o.autotune) {
+      switch (p) {
+        case STAG_FP64: s = tune_dslash<64>(lat, st); break;
+        case STAG_FP32: s = tune_dslash<32>(lat, st); break;
+        case STAG_FP16: s = tune_dslash<16>(lat, st); break;
+        default: s = tune_dslash<15>(lat, st);
+      }
+    }
     if (s) {
       stag_free_lattice(lat);
       return s;
@@ -255,6 +297,16 @@ int stag_free_lattice(stag_lattice_t lat) {
   for (auto& L : lat->links)
     if (L.data) cudaFree(L.data);
   delete lat;
+  return STAG_OK;
+}
+
+int stag_tuned_shape(stag_lattice_t lat, int prec, int kernel, int* block, int* min_blocks, double* us) {
+  if (!lat || prec < 0 || prec > 3 || kernel < 0 || kernel > 1 || !lat->links[prec].present) return STAG_EINVAL;
+  const LinkCopy& L = lat->links[prec];
+  int v = kernel == 0 ? L.shape_plain : L.shape_epi;
+  if (block) *block = v < 2 ? 256 : 128;
+  if (min_blocks) *min_blocks = v == 1 ? 4 : v == 3 ? 8 : 1;
+  if (us) *us = L.tuned_us[kernel];
   return STAG_OK;
 }
 

@@ -125,8 +125,8 @@ constexpr float FX_ONE = 32767.0f;  // fixed-point full scale
 
 // ---- 16-byte link chunks: complex numbers packed PER to a 16-byte word so
 // that every link load is a 128-bit load.  get() returns the stored value as
-// a normalised number (for the 16-bit formats: in [-1, 1], to be multiplied
-// by the field's scale).
+// a normalised number (binary16: in [-1, 1]; fixed point: the integer), to be
+// multiplied by the field's scale.
 template <int P> struct Chunk;
 template <> struct Chunk<64> {
   static constexpr int PER = 1;
@@ -150,8 +150,15 @@ __device__ __forceinline__ float2 half2_bits_to_float2(unsigned w) {
   r.y = (unsigned short)(w >> 16);
   return __half22float2(__half2(r));
 }
+// Two signed 16-bit integers (one 32-bit word) to floats without the
+// quarter-rate integer-to-float conversion: each half, biased by 2^15 (the
+// XOR), is placed in the low mantissa bits of 1.5 * 2^23, giving the exact
+// float 1.5 * 2^23 + 2^15 + q; one FP32 subtraction then yields q.
 __device__ __forceinline__ float2 short2_bits_to_float2(unsigned w) {
-  return make_float2((float)(short)(w & 0xffffu), (float)(short)(w >> 16));
+  const unsigned b = w ^ 0x80008000u;
+  const float lo = __uint_as_float(__byte_perm(b, 0x4B40u, 0x5410));
+  const float hi = __uint_as_float(__byte_perm(b, 0x4B40u, 0x5432));
+  return make_float2(__fadd_rn(lo, -12615680.0f), __fadd_rn(hi, -12615680.0f));
 }
 template <> struct Chunk<16> {
   static constexpr int PER = 4;
@@ -159,11 +166,12 @@ template <> struct Chunk<16> {
     return half2_bits_to_float2(word_of(c, lane));
   }
 };
+// Fixed point: get() returns the stored integer (as an exact float); the
+// 1/32767 joins the per-field scale applied after the hop sums.
 template <> struct Chunk<15> {
   static constexpr int PER = 4;
   static __device__ __forceinline__ float2 get(const uint4& c, int lane) {
-    float2 v = short2_bits_to_float2(word_of(c, lane));
-    return make_float2(v.x * (1.0f / FX_ONE), v.y * (1.0f / FX_ONE));
+    return short2_bits_to_float2(word_of(c, lane));
   }
 };
 
@@ -273,7 +281,10 @@ enum StateFlags : int {
   F_BREAKDOWN = 2,  // NaN/Inf or <p,Ap> <= 0
   F_NEED_RU = 4,    // reliable-update trigger
   F_ITER_CAP = 8,   // max_iter reached
-  F_STOP = F_CONVERGED | F_BREAKDOWN | F_ITER_CAP,
+  // Krylov-loop kernels queued after any of these return at once; the host
+  // then performs the reliable update (or stops) at the end of the chunk, so
+  // an update happens at the iteration that triggered it
+  F_STOP = F_CONVERGED | F_BREAKDOWN | F_ITER_CAP | F_NEED_RU,
 };
 
 // Scalars of one CG solve, resident in device memory and updated by the
@@ -449,6 +460,42 @@ __device__ inline void finalize(const RedTarget& t, const double* v, int nv) {
     }
   }
 }
+
+// ------------------------------------------------------------------ accurate sums
+// Per-thread dot-product accumulation in FP32 arithmetic with FP64-class
+// accuracy: each product is split exactly into p + e (e = fma(a, b, -p)) and
+// added to a (hi, lo) pair with Knuth's TwoSum, the error-free
+// transformations of Ogita, Rump and Oishi ("Accurate sum and dot product",
+// 2005).  GB300 executes FP64 at a small fraction of its FP32 rate, so the
+// per-element work stays on the FP32 pipes and only the per-thread result
+// enters the FP64 cross-thread tree.  The _rn intrinsics keep the compiler
+// from contracting the sums into FMAs, which would break the transformation.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ void df_add_prod(DF& acc, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fadd_rn(s, -acc.hi);
+  const float err = __fadd_rn(__fadd_rn(acc.hi, -__fadd_rn(s, -bb)), __fadd_rn(p, -bb));
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+}
+__device__ __forceinline__ double df_value(const DF& d) { return (double)d.hi + (double)d.lo; }
+
+// Accumulator selected by arithmetic type: FP64 sums for double, DF for float.
+template <class A> struct Acc1;
+template <> struct Acc1<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <> struct Acc1<float> {
+  DF v{0.f, 0.f};
+  __device__ __forceinline__ void add_prod(float a, float b) { df_add_prod(v, a, b); }
+  __device__ __forceinline__ double value() const { return df_value(v); }
+};
 
 // Deterministic block sum of NV doubles; the total is valid in thread 0.
 template <int NV> __device__ __forceinline__ void block_sum(double (&v)[NV]) {

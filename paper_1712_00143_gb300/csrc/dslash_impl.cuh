@@ -68,6 +68,11 @@ __device__ __forceinline__ void hop_recon12(A2 acc[3], const uint4 (&buf)[NCH], 
     A2 r2;
     r2.x = m[k].x * m[3 + l].x - m[k].y * m[3 + l].y - (m[l].x * m[3 + k].x - m[l].y * m[3 + k].y);
     r2.y = -(m[k].x * m[3 + l].y + m[k].y * m[3 + l].x - (m[l].x * m[3 + k].y + m[l].y * m[3 + k].x));
+    if (P == 15) {
+      // rows hold integers 32767 * entry: row 2 comes out 32767 times too large
+      r2.x *= 1.0f / FX_ONE;
+      r2.y *= 1.0f / FX_ONE;
+    }
     cmac(t[0], m[j], psi[j]);
     cmac(t[1], m[3 + j], psi[j]);
     cmac(t[2], r2, psi[j]);
@@ -170,8 +175,15 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<P>& a, int s, typen
   }
 }
 
-template <int P, int NL>
-__global__ void __launch_bounds__(256) k_dslash(DslashArgs<P> a, Spinor<P> out, const int* flags) {
+// Launch shapes the autotuner chooses among: threads per block and the
+// minimum number of resident blocks per SM promised to the compiler (which
+// caps registers per thread; 1 = no cap).
+constexpr int kNumShapes = 4;
+__host__ __device__ constexpr int shape_block(int v) { return v < 2 ? 256 : 128; }
+__host__ __device__ constexpr int shape_minb(int v) { return v == 1 ? 4 : v == 3 ? 8 : 1; }
+
+template <int P, int NL, int B, int MINB>
+__global__ void __launch_bounds__(B, MINB) k_dslash(DslashArgs<P> a, Spinor<P> out, const int* flags) {
   if (stopped(flags)) return;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.g.Vh) return;
@@ -182,8 +194,8 @@ __global__ void __launch_bounds__(256) k_dslash(DslashArgs<P> a, Spinor<P> out, 
 
 // out = ax x + ay y + ad (D in), with an FP64 reduction of Re<x,out> (RED=1)
 // or ||out||^2 (RED=2) finalised by the last block.
-template <int P, int NL, int RED>
-__global__ void __launch_bounds__(256)
+template <int P, int NL, int RED, int B, int MINB>
+__global__ void __launch_bounds__(B, MINB)
     k_dslash_epi(DslashArgs<P> a, Spinor<Acc<P>::value> out, Spinor<P> x, double ax, Spinor<Acc<P>::value> y,
                  double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags) {
   using A2 = typename Prec<P>::A2;
@@ -212,12 +224,14 @@ __global__ void __launch_bounds__(256)
       }
     }
     SpinorLoad<Acc<P>::value>::st(out, s, o);
-    if (RED == 1) {
+    if (RED) {
+      Acc1<A> acc;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) red[0] += (double)xv[i].x * (double)o[i].x + (double)xv[i].y * (double)o[i].y;
-    } else if (RED == 2) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) red[0] += (double)o[i].x * (double)o[i].x + (double)o[i].y * (double)o[i].y;
+      for (int i = 0; i < 3; ++i) {
+        acc.add_prod(RED == 1 ? xv[i].x : o[i].x, o[i].x);
+        acc.add_prod(RED == 1 ? xv[i].y : o[i].y, o[i].y);
+      }
+      red[0] = acc.value();
     }
   }
   if (RED) grid_reduce<1>(red, rb, tgt);
@@ -230,60 +244,167 @@ static DslashArgs<P> make_args(const stag_lattice_s* lat, Spinor<P> in, int out_
   a.g = lat->g;
   a.out_parity = out_parity;
   a.links = (const uint4*)((const char*)L.data + (size_t)out_parity * L.parity_stride);
-  a.fat_scale = L.fat_scale;
-  a.long_scale = L.nl == 6 ? (float)(0.5 * lat->c3) : L.long_scale;
+  const double fx = P == 15 ? 1.0 / 32767.0 : 1.0;  // fixed point: integers -> entries
+  a.fat_scale = (float)(L.fat_scale * fx);
+  a.long_scale = (float)((L.nl == 6 ? 0.5 * lat->c3 : (double)L.long_scale) * fx);
   a.in = in;
   return a;
+}
+
+template <int P, int NL>
+static void dispatch_plain(int shape, const DslashArgs<P>& a, Spinor<P> out, const int* flags, cudaStream_t st) {
+  const int Vh = a.g.Vh;
+#define STAG_PL(V)                                                                                \
+  k_dslash<P, NL, shape_block(V), shape_minb(V)>                                                  \
+      <<<(Vh + shape_block(V) - 1) / shape_block(V), shape_block(V), 0, st>>>(a, out, flags)
+  switch (shape) {
+    case 1: STAG_PL(1); break;
+    case 2: STAG_PL(2); break;
+    case 3: STAG_PL(3); break;
+    default: STAG_PL(0);
+  }
+#undef STAG_PL
+}
+
+template <int P, int NL, int RED>
+static void dispatch_epi(int shape, const DslashArgs<P>& a, Spinor<Acc<P>::value> out, Spinor<P> x, double ax,
+                         Spinor<Acc<P>::value> y, double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags,
+                         cudaStream_t st) {
+  const int Vh = a.g.Vh;
+#define STAG_EP(V)                                                                                \
+  k_dslash_epi<P, NL, RED, shape_block(V), shape_minb(V)>                                         \
+      <<<(Vh + shape_block(V) - 1) / shape_block(V), shape_block(V), 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags)
+  switch (shape) {
+    case 1: STAG_EP(1); break;
+    case 2: STAG_EP(2); break;
+    case 3: STAG_EP(3); break;
+    default: STAG_EP(0);
+  }
+#undef STAG_EP
+}
+
+template <int P>
+static int plain_with_shape(const stag_lattice_s* lat, int shape, Spinor<P> out, Spinor<P> in, int out_parity,
+                            const int* flags, cudaStream_t st) {
+  const LinkCopy& L = lat->links[prec_index<P>()];
+  DslashArgs<P> a = make_args<P>(lat, in, out_parity);
+  constexpr int NL2 = P == 64 ? 9 : 6;
+  if (P == 64 || L.nl == 9)
+    dispatch_plain<P, 9>(shape, a, out, flags, st);
+  else
+    dispatch_plain<P, NL2>(shape, a, out, flags, st);
+  return last_launch_status();
+}
+
+template <int P>
+static int epi_with_shape(const stag_lattice_s* lat, int shape, Spinor<Acc<P>::value> out, Spinor<P> in,
+                          int out_parity, Spinor<P> x, double ax, Spinor<Acc<P>::value> y, double ay, double ad,
+                          int red, RedScratch rs, RedTarget tgt, const int* flags, cudaStream_t st) {
+  const LinkCopy& L = lat->links[prec_index<P>()];
+  DslashArgs<P> a = make_args<P>(lat, in, out_parity);
+  const int G = (lat->g.Vh + shape_block(shape) - 1) / shape_block(shape);
+  if (red && G > rs.max_grid) return STAG_EINVAL;
+  RedBuf rb{rs.partials, rs.counter};
+  constexpr int NL2 = P == 64 ? 9 : 6;
+  const bool r12 = P != 64 && L.nl == 6;
+#define STAG_E(NL, R) dispatch_epi<P, NL, R>(shape, a, out, x, ax, y, ay, ad, rb, tgt, flags, st)
+  if (r12) {
+    if (red == 0) STAG_E(NL2, 0);
+    else if (red == 1) STAG_E(NL2, 1);
+    else STAG_E(NL2, 2);
+  } else {
+    if (red == 0) STAG_E(9, 0);
+    else if (red == 1) STAG_E(9, 1);
+    else STAG_E(9, 2);
+  }
+#undef STAG_E
+  return last_launch_status();
 }
 
 template <int P>
 int launch_dslash(const stag_lattice_s* lat, Spinor<P> out, Spinor<P> in, int out_parity, const int* flags,
                   cudaStream_t st) {
-  const int pi = prec_index<P>();
-  if (!lat->links[pi].present) return STAG_EINVAL;
-  DslashArgs<P> a = make_args<P>(lat, in, out_parity);
-  const int B = 256;
-  const int G = (lat->g.Vh + B - 1) / B;
+  const LinkCopy& L = lat->links[prec_index<P>()];
+  if (!L.present) return STAG_EINVAL;
   ProfScope ps("dslash", st);
-  if (P == 64 || lat->links[pi].nl == 9)
-    k_dslash<P, 9><<<G, B, 0, st>>>(a, out, flags);
-  else
-    k_dslash<P, (P == 64 ? 9 : 6)><<<G, B, 0, st>>>(a, out, flags);
-  return last_launch_status();
+  return plain_with_shape<P>(lat, L.shape_plain, out, in, out_parity, flags, st);
 }
 
 template <int P>
 int launch_dslash_epi(const stag_lattice_s* lat, Spinor<Acc<P>::value> out, Spinor<P> in, int out_parity,
                       Spinor<P> x, double ax, Spinor<Acc<P>::value> y, double ay, double ad, int red,
                       RedScratch rs, RedTarget tgt, const int* flags, cudaStream_t st) {
-  const int pi = prec_index<P>();
-  if (!lat->links[pi].present) return STAG_EINVAL;
-  DslashArgs<P> a = make_args<P>(lat, in, out_parity);
-  const int B = 256;
-  const int G = (lat->g.Vh + B - 1) / B;
-  if (red && G > rs.max_grid) return STAG_EINVAL;
-  RedBuf rb{rs.partials, rs.counter};
+  const LinkCopy& L = lat->links[prec_index<P>()];
+  if (!L.present) return STAG_EINVAL;
   ProfScope ps("dslash_epi", st);
-  const bool r12 = P != 64 && lat->links[pi].nl == 6;
-  constexpr int NL2 = P == 64 ? 9 : 6;
-#define STAG_EPI(NL, R) k_dslash_epi<P, NL, R><<<G, B, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags)
-  if (r12) {
-    if (red == 0) STAG_EPI(NL2, 0);
-    else if (red == 1) STAG_EPI(NL2, 1);
-    else STAG_EPI(NL2, 2);
-  } else {
-    if (red == 0) STAG_EPI(9, 0);
-    else if (red == 1) STAG_EPI(9, 1);
-    else STAG_EPI(9, 2);
+  return epi_with_shape<P>(lat, L.shape_epi, out, in, out_parity, x, ax, y, ay, ad, red, rs, tgt, flags, st);
+}
+
+// Autotuner: times every launch shape of the plain and the fused-epilogue
+// (dot-product) kernel on this lattice and precision, on scratch vectors,
+// and keeps the fastest of each in the link copy.  Runs once per gauge field.
+template <int P>
+int tune_dslash(stag_lattice_s* lat, cudaStream_t st) {
+  constexpr int PA = Acc<P>::value;
+  LinkCopy& L = lat->links[prec_index<P>()];
+  if (!L.present) return STAG_EINVAL;
+  int s = 0;
+  Spinor<P> in = ws_spinor<P>(lat, "tune.in", &s);
+  Spinor<P> out = ws_spinor<P>(lat, "tune.out", &s);
+  Spinor<PA> o = ws_spinor<PA>(lat, "tune.o", &s);
+  double* scal = (double*)lat->ws.get("tune.scalar", 64, &s);
+  if (s) return s;
+  RedScratch rs;
+  if ((s = get_red_scratch(lat, "tune", &rs))) return s;
+  if ((s = cuda_status(cudaMemsetAsync(in.v, 0, spinor_bytes<P>(in.Vh), st)))) return s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return STAG_ECUDA;
   }
-#undef STAG_EPI
-  return last_launch_status();
+  const int reps = 5;
+  float best[2] = {1e30f, 1e30f};
+  int pick[2] = {0, 0};
+  for (int kind = 0; kind < 2 && !s; ++kind) {
+    for (int v = 0; v < kNumShapes && !s; ++v) {
+      for (int it = -2; it < reps && !s; ++it) {
+        if (it == 0) s = cuda_status(cudaEventRecord(e0, st));
+        if (s) break;
+        count_launch();
+        s = kind == 0 ? plain_with_shape<P>(lat, v, out, in, 1, nullptr, st)
+                      : epi_with_shape<P>(lat, v, o, out, 0, in, 1.0, Spinor<PA>{nullptr, in.Vh}, 0.0, -1.0, 1, rs,
+                                          RedTarget{RED_STORE, nullptr, scal}, nullptr, st);
+      }
+      if (s) break;
+      float ms = 0.f;
+      if ((s = cuda_status(cudaEventRecord(e1, st)))) break;
+      if ((s = cuda_status(cudaEventSynchronize(e1)))) break;
+      if ((s = cuda_status(cudaEventElapsedTime(&ms, e0, e1)))) break;
+      if (ms < best[kind]) {
+        best[kind] = ms;
+        pick[kind] = v;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  lat->ws.drop("tune.in");
+  lat->ws.drop("tune.out");
+  lat->ws.drop("tune.o");
+  if (s) return s;
+  L.shape_plain = pick[0];
+  L.shape_epi = pick[1];
+  L.tuned_us[0] = best[0] * 1e3f / reps;
+  L.tuned_us[1] = best[1] * 1e3f / reps;
+  return STAG_OK;
 }
 
 #define STAG_INSTANTIATE_DSLASH(P)                                                                          \
   template int launch_dslash<P>(const stag_lattice_s*, Spinor<P>, Spinor<P>, int, const int*, cudaStream_t); \
   template int launch_dslash_epi<P>(const stag_lattice_s*, Spinor<Acc<P>::value>, Spinor<P>, int, Spinor<P>, \
                                     double, Spinor<Acc<P>::value>, double, double, int, RedScratch, RedTarget, \
-                                    const int*, cudaStream_t);
+                                    const int*, cudaStream_t);                                              \
+  template int tune_dslash<P>(stag_lattice_s*, cudaStream_t);
 
 }  // namespace stag

@@ -25,6 +25,9 @@ struct LinkCopy {
   float fat_scale = 1.f;    // 16-bit formats: stored (normalised) value * scale
   float long_scale = 1.f;   //   = matrix entry
   size_t elem_bytes = 0;    // bytes of one stored complex
+  int shape_plain = 1;      // launch shapes chosen by the autotuner
+  int shape_epi = 1;        // (default: 256 threads, 4 blocks per SM)
+  float tuned_us[2] = {0.f, 0.f};  // their timings (us per launch)
 };
 
 struct Workspace {
@@ -33,6 +36,7 @@ struct Workspace {
   // Device buffer of at least `bytes` bytes under `name` (contents kept only
   // while the size does not grow; *fresh set when newly allocated).
   void* get(const std::string& name, size_t bytes, int* status, bool* fresh = nullptr);
+  void drop(const std::string& name);
   void release();
 };
 
@@ -93,6 +97,9 @@ template <int P>
 int launch_dslash(const stag_lattice_s* lat, Spinor<P> out, Spinor<P> in, int out_parity, const int* flags,
                   cudaStream_t st);
 
+// Times the launch shapes of the Dslash kernels and keeps the fastest.
+template <int P> int tune_dslash(stag_lattice_s* lat, cudaStream_t st);
+
 // out = ax * x + ay * y + ad * (D in) on parity out_parity, and optionally a
 // reduction: red = 1: Re <x, out>; red = 2: ||out||^2.
 template <int P>
@@ -134,7 +141,7 @@ int launch_ms_r_update(Spinor<Acc<P>::value> r, Spinor<Acc<P>::value> Ap, MsStat
 // Runs only when the state's iteration count equals expect_iter (the residual
 // update of this iteration ran); `base` is the smallest shift.
 template <int P>
-int launch_ms_shift_update(Spinor<64>* xs, Spinor<P>* ps, int nshift, int base, Spinor<Acc<P>::value> r,
+int launch_ms_shift_update(Spinor<Acc<P>::value>* xs, Spinor<P>* ps, int nshift, int base, Spinor<Acc<P>::value> r,
                            MsState* state, int expect_iter, cudaStream_t st);
 
 }  // namespace stag

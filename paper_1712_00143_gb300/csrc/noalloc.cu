@@ -64,12 +64,12 @@ extern "C" int stag_apply_m_noalloc(stag_lattice_t lat, void* out, const void* i
   // t = D_oe in (odd sites): every entry of t is written before it is read
   DslashArgs<64> a1 = make_args<64>(lat, x, 1);
   count_launch();
-  k_dslash<64, 9><<<G, B, 0, st>>>(a1, t, nullptr);
+  k_dslash<64, 9, 256, 1><<<G, B, 0, st>>>(a1, t, nullptr);
   if ((s = last_launch_status())) return s;
   // out = (m^2 + shift) in - D_eo t (even sites)
   DslashArgs<64> a2 = make_args<64>(lat, t, 0);
   count_launch();
-  k_dslash_epi<64, 9, 0><<<G, B, 0, st>>>(a2, o, x, mass * mass + shift, none, 0.0, -1.0, RedBuf{nullptr, nullptr},
+  k_dslash_epi<64, 9, 0, 256, 1><<<G, B, 0, st>>>(a2, o, x, mass * mass + shift, none, 0.0, -1.0, RedBuf{nullptr, nullptr},
                                           RedTarget{RED_STORE, nullptr, nullptr}, nullptr);
   return last_launch_status();
 }

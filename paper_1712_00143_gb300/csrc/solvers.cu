@@ -200,9 +200,10 @@ static int cg_solve(stag_lattice_s* lat, double2* x_can, const double2* b_can, d
   return status;
 }
 
-// Multi-shift CG in sloppy precision P with FP64 solution vectors, followed
-// by a per-shift CG refinement of every shift whose FP64 true residual misses
-// the target.
+// Multi-shift CG in sloppy precision P (solution vectors in the loop's vector
+// precision: FP64 for P = 64, FP32 otherwise), followed by a per-shift CG
+// refinement, accumulated in FP64, of every shift whose FP64 true residual
+// misses the target.
 template <int P>
 static int ms_solve(stag_lattice_s* lat, double2* const* x_can, const double2* b_can, double mass,
                     const double* shifts, int ns, const stag_solve_params& prm, stag_solve_info* infos,
@@ -218,10 +219,10 @@ static int ms_solve(stag_lattice_s* lat, double2* const* x_can, const double2* b
   Spinor<PV> r = ws_spinor<PV>(lat, "ms.r", &s);
   Spinor<PV> Ap = ws_spinor<PV>(lat, "ms.Ap", &s);
   Spinor<P> t = ws_spinor<P>(lat, "ms.t", &s);
-  std::vector<Spinor<64>> xs(ns);
+  std::vector<Spinor<PV>> xs(ns);
   std::vector<Spinor<P>> ps(ns);
   for (int k = 0; k < ns; ++k) {
-    xs[k] = ws_spinor<64>(lat, "ms.x" + std::to_string(k), &s);
+    xs[k] = ws_spinor<PV>(lat, "ms.x" + std::to_string(k), &s);
     ps[k] = ws_spinor<P>(lat, "ms.p" + std::to_string(k), &s);
   }
   MsState* dst = (MsState*)lat->ws.get("ms.state", sizeof(MsState), &s);
@@ -272,7 +273,7 @@ static int ms_solve(stag_lattice_s* lat, double2* const* x_can, const double2* b
   TRY(cuda_status(cudaMemcpyAsync(dst, hs, sizeof(MsState), cudaMemcpyHostToDevice, st)));
   TRY(launch_convert<PV, 64>(r, b64, st));
   for (int k = 0; k < ns; ++k) {
-    TRY(launch_zero(xs[k].v, spinor_bytes<64>(Vh), st));
+    TRY(launch_zero(xs[k].v, spinor_bytes<PV>(Vh), st));
     TRY(launch_convert<P, 64>(ps[k], b64, st));
   }
   int status = STAG_OK;
@@ -305,7 +306,7 @@ static int ms_solve(stag_lattice_s* lat, double2* const* x_can, const double2* b
   h = *hs;
   // per-shift verification and refinement from x_s
   int worst = status;
-  for (int k = 0; k < ns; ++k) TRY(launch_to_canonical<64>(x_can[k], xs[k], Vh, st));
+  for (int k = 0; k < ns; ++k) TRY(launch_to_canonical<PV>(x_can[k], xs[k], Vh, st));
   if (status == STAG_OK) {
     stag_solve_params rp = prm;
     rp.use_initial_guess = 1;

@@ -189,6 +189,16 @@ def test_sampled_sites_match_full_apply():
     assert np.array_equal(oracle.dslash(fat, lng, psi, dims, 1, out_sites=sites), full[sites])
 
 
+def test_apply_m_at_sites_matches_full_apply():
+    dims = (4, 6, 4, 8)
+    fat, lng = synth.gauge_field(dims, 0.3, 1008)
+    v = synth.random_spinor(dims, 12)
+    full = oracle.apply_m(fat, lng, v, 0.07, dims, shift=0.03)
+    sites = np.array([0, 3, 50, 191])
+    part = oracle.apply_m_at_sites(fat, lng, v, 0.07, dims, sites, shift=0.03)
+    assert np.abs(part - full[sites]).max() < 1e-14
+
+
 # --------------------------------------------------------------- solver pins
 
 
