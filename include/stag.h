@@ -187,6 +187,29 @@ int stag_multishift_cg(stag_lattice_t lat, void* const* x, const void* b, double
                        const double* shifts, int nshift, const stag_solve_params* params,
                        stag_solve_info* infos, void* stream);
 
+/* One lattice's share of a batched solve: nrhs systems M x_i = b_i with the
+ * same mass.  x, b: device, canonical [nrhs][V/2][3] complex double. */
+typedef struct {
+  stag_lattice_t lat;
+  void* x;
+  const void* b;
+  int nrhs;
+  double mass;
+} stag_batch_item;
+
+/* Solve every system of every item to params->tol (FP64 true residual), all
+ * items together: each item's right-hand sides are solved in groups of up to
+ * 8 that share one multi-right-hand-side Dslash per operator application
+ * (links read once for the whole group), each system with its own CG
+ * scalars and its own stopping point; the groups of all items advance side
+ * by side, one CUDA graph launch per chunk of check_interval iterations.
+ * Modes as for stag_cg (use_initial_guess reads x).  infos: host array with
+ * one entry per system, item by item, may be NULL.  Returns STAG_OK, or the
+ * first error (ENOTCONV, EBREAKDOWN ...) met by a system.  Synchronises
+ * `stream`. */
+int stag_batch_solve(const stag_batch_item* items, int nitems, const stag_solve_params* params,
+                     stag_solve_info* infos, void* stream);
+
 /* Human-readable text of a status code (static storage). */
 const char* stag_strerror(int status);
 

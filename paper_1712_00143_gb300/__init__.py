@@ -48,6 +48,7 @@ EXPORTS = (
     "stag_apply_m_noalloc",
     "stag_cg",
     "stag_multishift_cg",
+    "stag_batch_solve",
     "stag_strerror",
     "stag_profile_enable",
     "stag_profile_select",
@@ -81,6 +82,16 @@ class SolveParams(ctypes.Structure):
         ("use_initial_guess", ctypes.c_int),
         ("check_interval", ctypes.c_int),
         ("ms_tol", ctypes.c_double),
+    ]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [
+        ("lat", ctypes.c_void_p),
+        ("x", ctypes.c_void_p),
+        ("b", ctypes.c_void_p),
+        ("nrhs", ctypes.c_int),
+        ("mass", ctypes.c_double),
     ]
 
 
@@ -120,6 +131,7 @@ def load_library(path=LIB_PATH):
             ci,
             [vp, ctypes.POINTER(vp), vp, cd, ctypes.POINTER(cd), ci, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), vp],
         ),
+        "stag_batch_solve": (ci, [ctypes.POINTER(BatchItem), ci, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), vp]),
         "stag_strerror": (ctypes.c_char_p, [ci]),
         "stag_profile_enable": (ci, [ci]),
         "stag_profile_select": (ci, [ctypes.c_char_p, ci]),
@@ -290,6 +302,28 @@ def stag_multishift_cg(h, xs, b, mass, shifts, params=None, stream=None, raise_o
     st = _lib.stag_multishift_cg(h.ptr, ptrs, _ptr(b, "b", n), float(mass), sh, ns, ctypes.byref(p), infos, _stream(stream))
     if raise_on_error and st != STAG_OK:
         raise StagError(st, "stag_multishift_cg")
+    out = [i.as_dict() for i in infos]
+    for d in out:
+        d["return"] = st
+    return out
+
+
+def stag_batch_solve(items, params=None, stream=None, raise_on_error=True, **kw):
+    """Solve many systems on several lattices together.
+
+    items: sequence of (handle, x, b, nrhs, mass) with x, b complex128 CUDA
+    tensors [nrhs][V/2][3].  Returns one info dict per system, item by item."""
+    p = params if params is not None else default_params(**kw)
+    arr = (BatchItem * len(items))()
+    total = 0
+    for i, (h, x, b, nrhs, mass) in enumerate(items):
+        n = h.Vh * 3 * int(nrhs)
+        arr[i] = BatchItem(h.ptr.value, _ptr(x, f"x[{i}]", n).value, _ptr(b, f"b[{i}]", n).value, int(nrhs), float(mass))
+        total += int(nrhs)
+    infos = (SolveInfo * total)()
+    st = _lib.stag_batch_solve(arr, len(items), ctypes.byref(p), infos, _stream(stream))
+    if raise_on_error and st != STAG_OK:
+        raise StagError(st, "stag_batch_solve")
     out = [i.as_dict() for i in infos]
     for d in out:
         d["return"] = st

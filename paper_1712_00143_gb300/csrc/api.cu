@@ -46,12 +46,12 @@ void Workspace::drop(const std::string& name) {
   bufs.erase(it);
 }
 
-int get_red_scratch(stag_lattice_s* lat, const char* name, RedScratch* out) {
+int get_red_scratch(stag_lattice_s* lat, const char* name, RedScratch* out, int nv_max) {
   int st = 0;
   int max_grid = (lat->g.Vh + 127) / 128;  // one block per 128 sites at most
   if (max_grid < 1024) max_grid = 1024;
   std::string n(name);
-  double* p = (double*)lat->ws.get(n + ".partials", sizeof(double) * 2 * (size_t)max_grid, &st);
+  double* p = (double*)lat->ws.get(n + ".partials", sizeof(double) * (size_t)nv_max * (size_t)max_grid, &st);
   if (st) return st;
   bool fresh = false;
   unsigned* c = (unsigned*)lat->ws.get(n + ".counter", 256, &st, &fresh);
@@ -134,7 +134,22 @@ void flush_locked(bool wait) {
 }
 }  // namespace
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+thread_local bool t_capturing = false;
+thread_local long long t_captured = 0;
+
+void count_launch() {
+  if (t_capturing)
+    ++t_captured;
+  else
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+long long set_capturing(bool on) {
+  long long n = t_captured;
+  t_capturing = on;
+  t_captured = 0;
+  return n;
+}
 
 bool family_selected(const char* family) {
   if (g_filter.empty()) return true;
@@ -151,7 +166,7 @@ bool family_selected(const char* family) {
 
 void prof_begin(const char* family, cudaStream_t s) {
   t_pending = -1;
-  if (!g_prof) return;
+  if (!g_prof || t_capturing) return;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!family_selected(family)) return;
   if (g_every > 1 && (g_seen[family]++ % g_every) != 0) return;
@@ -378,6 +393,7 @@ int stag_dslash(stag_lattice_t lat, void* out, const void* in, int out_parity, i
   if (!lat || !out || !in || (out_parity != 0 && out_parity != 1) || nrhs < 1) return STAG_EINVAL;
   if (prec < 0 || prec > 3 || !lat->links[prec].present) return STAG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  if (nrhs > 1) return dslash_multi(lat, (double2*)out, (const double2*)in, out_parity, prec, nrhs, st);
   switch (prec) {
     case STAG_FP64: return dslash_p<64>(lat, (double2*)out, (const double2*)in, out_parity, nrhs, st);
     case STAG_FP32: return dslash_p<32>(lat, (double2*)out, (const double2*)in, out_parity, nrhs, st);

@@ -1,0 +1,597 @@
+// batch.cu -- many CG systems at once: the N-right-hand-side Dslash behind
+// stag_dslash(nrhs > 1), and stag_batch_solve, which runs the systems of
+// several lattices together.
+//
+// A lattice's right-hand sides are solved in groups of N = 8, 4 or 2 systems
+// that share one N-RHS Dslash per application (links read once for N
+// vectors); every system keeps its own CG scalars (McgState) and leaves the
+// iteration when its residual reaches the target.  The groups of all
+// lattices advance together: each group owns a stream, and the chunk of
+// `check_interval` iterations of every group is captured once into one CUDA
+// graph (fork from the caller's stream, one branch per group, join) that is
+// replayed until the groups finish, so independent lattices of uneven sizes
+// fill the GPU side by side and a chunk costs one graph launch.  Reliable
+// updates (FP64 true residual of every system of a group) run between chunks
+// for the groups that ask for them.
+#include <chrono>
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "batch_kernels.cuh"
+
+namespace stag {
+
+namespace {
+
+#define TRYB(...)              \
+  do {                         \
+    int _s = (__VA_ARGS__);    \
+    if (_s) return _s;         \
+  } while (0)
+
+int sm_count_b() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else {
+      cudaGetLastError();
+      n = 152;
+    }
+  }
+  return n;
+}
+int grid_red(int Vh, int cap) {
+  int g = (Vh + 255) / 256, m = 4 * sm_count_b();
+  g = g < m ? g : m;
+  return g < cap ? g : cap;
+}
+int grid_bw(int Vh) {
+  int g = (Vh + 255) / 256, m = 8 * sm_count_b();
+  return g < m ? g : m;
+}
+
+template <int P> DslashArgsM<P> make_args_m(const stag_lattice_s* lat, SpinorM<P> in, int out_parity) {
+  const LinkCopy& L = lat->links[prec_index<P>()];
+  DslashArgsM<P> a;
+  a.g = lat->g;
+  a.out_parity = out_parity;
+  a.links = (const uint4*)((const char*)L.data + (size_t)out_parity * L.parity_stride);
+  const double fx = P == 15 ? 1.0 / 32767.0 : 1.0;
+  a.fat_scale = (float)(L.fat_scale * fx);
+  a.long_scale = (float)((L.nl == 6 ? 0.5 * lat->c3 : (double)L.long_scale) * fx);
+  a.in = in;
+  return a;
+}
+
+}  // namespace
+
+template <int P, int N>
+int mdslash(const stag_lattice_s* lat, SpinorM<P> out, SpinorM<P> in, int out_parity, const int* flags,
+            cudaStream_t st) {
+  const LinkCopy& L = lat->links[prec_index<P>()];
+  if (!L.present) return STAG_EINVAL;
+  DslashArgsM<P> a = make_args_m<P>(lat, in, out_parity);
+  const int G = (lat->g.Vh + MB - 1) / MB;
+  ProfScope ps("dslash_mrhs", st);
+  if (P == 64 || L.nl == 9)
+    k_dslash_m<P, 9, N><<<G, MB, 0, st>>>(a, out, flags);
+  else
+    k_dslash_m<P, (P == 64 ? 9 : 6), N><<<G, MB, 0, st>>>(a, out, flags);
+  return last_launch_status();
+}
+
+template <int P, int N, int RED>
+int mdslash_epi(const stag_lattice_s* lat, SpinorM<Acc<P>::value> out, SpinorM<P> in, int out_parity, SpinorM<P> x,
+                double ax, SpinorM<Acc<P>::value> y, double ay, double ad, RedScratch rs, RedTarget tgt,
+                const int* flags, cudaStream_t st) {
+  const LinkCopy& L = lat->links[prec_index<P>()];
+  if (!L.present) return STAG_EINVAL;
+  DslashArgsM<P> a = make_args_m<P>(lat, in, out_parity);
+  const int G = (lat->g.Vh + MB - 1) / MB;
+  if (RED && G > rs.max_grid) return STAG_EINVAL;
+  ProfScope ps("dslash_mrhs_epi", st);
+  RedBuf rb{rs.partials, rs.counter};
+  if (P == 64 || L.nl == 9)
+    k_dslash_m_epi<P, 9, N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
+  else
+    k_dslash_m_epi<P, (P == 64 ? 9 : 6), N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
+  return last_launch_status();
+}
+
+template <int P> SpinorM<P> ws_spinorm(stag_lattice_s* lat, const std::string& name, int n, int* status) {
+  SpinorM<P> f;
+  f.Vh = lat->g.Vh;
+  f.n = n;
+  f.v = lat->ws.get(name, spinorm_bytes<P>(f.Vh, n), status);
+  return f;
+}
+
+// ------------------------------------------------------------ stag_dslash, nrhs > 1
+template <int P, int N>
+static int dslash_group(stag_lattice_s* lat, double2* out, const double2* in, int out_parity, cudaStream_t st) {
+  int s = 0;
+  SpinorM<P> a = ws_spinorm<P>(lat, "mdslash.in", N, &s);
+  SpinorM<P> b = ws_spinorm<P>(lat, "mdslash.out", N, &s);
+  if (s) return s;
+  {
+    ProfScope ps("convert", st);
+    k_mfrom_canonical<P, N><<<grid_bw(lat->g.Vh), 256, 0, st>>>(a, in, N);
+  }
+  TRYB(last_launch_status());
+  TRYB((mdslash<P, N>(lat, b, a, out_parity, nullptr, st)));
+  {
+    ProfScope ps("convert", st);
+    k_mto_canonical<P, N><<<grid_bw(lat->g.Vh), 256, 0, st>>>(out, b, N);
+  }
+  return last_launch_status();
+}
+
+template <int P>
+static int dslash_multi_p(stag_lattice_s* lat, double2* out, const double2* in, int out_parity, int nrhs,
+                          cudaStream_t st) {
+  const size_t n = (size_t)lat->g.Vh * 3;
+  int r = 0;
+  while (r < nrhs) {
+    const int left = nrhs - r;
+    int s;
+    if (left >= 8) s = dslash_group<P, 8>(lat, out + r * n, in + r * n, out_parity, st), r += 8;
+    else if (left >= 4) s = dslash_group<P, 4>(lat, out + r * n, in + r * n, out_parity, st), r += 4;
+    else if (left >= 2) s = dslash_group<P, 2>(lat, out + r * n, in + r * n, out_parity, st), r += 2;
+    else break;
+    if (s) return s;
+  }
+  if (r < nrhs) return stag_dslash(lat, out + r * n, in + r * n, out_parity, prec_index<P>(), 1, st);
+  return STAG_OK;
+}
+
+int dslash_multi(stag_lattice_s* lat, double2* out, const double2* in, int out_parity, int prec, int nrhs,
+                 cudaStream_t st) {
+  switch (prec) {
+    case STAG_FP64: return dslash_multi_p<64>(lat, out, in, out_parity, nrhs, st);
+    case STAG_FP32: return dslash_multi_p<32>(lat, out, in, out_parity, nrhs, st);
+    case STAG_FP16: return dslash_multi_p<16>(lat, out, in, out_parity, nrhs, st);
+    default: return dslash_multi_p<15>(lat, out, in, out_parity, nrhs, st);
+  }
+}
+
+// ------------------------------------------------------------ batched CG
+struct GroupBase {
+  stag_lattice_s* lat = nullptr;
+  double shift = 0.0;  // m^2
+  double2* x = nullptr;        // canonical, first system of the group
+  const double2* b = nullptr;
+  int nreal = 0;               // systems of the item in this group (<= N)
+  int item = 0, first = 0;     // item index and first right-hand side
+  cudaStream_t st = nullptr;
+  McgState* dst = nullptr;
+  McgState* hst = nullptr;     // pinned host copy
+  double* dscal = nullptr;     // device: bb[N], rr0[N]
+  double* hscal = nullptr;     // pinned
+  bool pending_p = false, done = false;
+  int status = STAG_OK;
+  double bb[MAX_RHS] = {0};
+  virtual ~GroupBase() {}
+  virtual int n() const = 0;
+  virtual int setup(const stag_solve_params& prm) = 0;
+  virtual int start(const stag_solve_params& prm) = 0;
+  virtual int iterations(int C) = 0;
+  virtual int reliable_update() = 0;
+  virtual int finish() = 0;
+};
+
+template <int P, int N> struct Group : GroupBase {
+  static constexpr int PV = Acc<P>::value;
+  SpinorM<64> b64, y64, r64, t64;
+  SpinorM<P> p, t;
+  SpinorM<PV> Ap, xh, rh;
+  RedScratch rs;
+  int n() const override { return N; }
+
+  int alloc(int gid) {
+    int s = 0;
+    const std::string pre = "batch" + std::to_string(gid) + ".";
+    b64 = ws_spinorm<64>(lat, pre + "b", N, &s);
+    y64 = ws_spinorm<64>(lat, pre + "y", N, &s);
+    r64 = ws_spinorm<64>(lat, pre + "r64", N, &s);
+    t64 = ws_spinorm<64>(lat, pre + "t64", N, &s);
+    p = ws_spinorm<P>(lat, pre + "p", N, &s);
+    t = ws_spinorm<P>(lat, pre + "t", N, &s);
+    Ap = ws_spinorm<PV>(lat, pre + "Ap", N, &s);
+    xh = ws_spinorm<PV>(lat, pre + "xh", N, &s);
+    rh = ws_spinorm<PV>(lat, pre + "rh", N, &s);
+    dst = (McgState*)lat->ws.get(pre + "state", sizeof(McgState), &s);
+    dscal = (double*)lat->ws.get(pre + "scal", sizeof(double) * 2 * MAX_RHS, &s);
+    if (s) return s;
+    return get_red_scratch(lat, (pre + "red").c_str(), &rs, 2 * N);
+  }
+
+  // FP64: r = b - shift y + D_eo D_oe y, ||r_i||^2 -> tgt
+  int true_residual(RedTarget tgt) {
+    TRYB((mdslash<64, N>(lat, t64, y64, 1, nullptr, st)));
+    return mdslash_epi<64, N, 2>(lat, r64, t64, 0, y64, -shift, b64, 1.0, 1.0, rs, tgt, nullptr, st);
+  }
+
+  int setup(const stag_solve_params& prm) override {
+    {
+      ProfScope ps("convert", st);
+      k_mfrom_canonical<64, N><<<grid_bw(lat->g.Vh), 256, 0, st>>>(b64, b, nreal);
+    }
+    TRYB(last_launch_status());
+    {
+      ProfScope ps("reduce", st);
+      k_mnorm2<64, N><<<grid_red(lat->g.Vh, rs.max_grid), 256, 0, st>>>(b64, RedBuf{rs.partials, rs.counter},
+                                                                         RedTarget{RED_STORE, nullptr, dscal});
+    }
+    TRYB(last_launch_status());
+    if (prm.use_initial_guess) {
+      {
+        ProfScope ps("convert", st);
+        k_mfrom_canonical<64, N><<<grid_bw(lat->g.Vh), 256, 0, st>>>(y64, x, nreal);
+      }
+      TRYB(last_launch_status());
+      TRYB(true_residual(RedTarget{RED_STORE, nullptr, dscal + MAX_RHS}));
+    } else {
+      TRYB(cuda_status(cudaMemsetAsync(y64.v, 0, spinorm_bytes<64>(lat->g.Vh, N), st)));
+      TRYB(cuda_status(cudaMemcpyAsync(r64.v, b64.v, spinorm_bytes<64>(lat->g.Vh, N), cudaMemcpyDeviceToDevice, st)));
+      TRYB(cuda_status(cudaMemcpyAsync(dscal + MAX_RHS, dscal, sizeof(double) * N, cudaMemcpyDeviceToDevice, st)));
+    }
+    return cuda_status(cudaMemcpyAsync(hscal, dscal, sizeof(double) * 2 * MAX_RHS, cudaMemcpyDeviceToHost, st));
+  }
+
+  // host state from the norms; sloppy copies rh = r, xh = 0, p = rh
+  int start(const stag_solve_params& prm) override {
+    McgState h{};
+    h.n = N;
+    h.max_iter = prm.max_iter;
+    int active = 0;
+    for (int i = 0; i < N; ++i) {
+      CgState& c = h.sys[i];
+      bb[i] = hscal[i];
+      const double rr0 = hscal[MAX_RHS + i];
+      c.rr = c.rr_prev = c.rr_max = c.rr_true = rr0;
+      c.target = prm.tol * prm.tol * bb[i];
+      c.delta2 = (P == 64) ? 0.0 : prm.delta * prm.delta;
+      c.shift = shift;
+      c.max_iter = prm.max_iter;
+      if (i < nreal && bb[i] > 0.0 && rr0 > c.target) active |= 1 << i;
+    }
+    h.active = active;
+    if (active == 0 || prm.max_iter <= 0) h.flags = F_CONVERGED;
+    *hst = h;
+    TRYB(cuda_status(cudaMemcpyAsync(dst, hst, sizeof(McgState), cudaMemcpyHostToDevice, st)));
+    const int G = grid_bw(lat->g.Vh);
+    {
+      ProfScope ps("convert", st);
+      k_mconvert<PV, 64, N><<<G, 256, 0, st>>>(rh, r64);
+    }
+    TRYB(last_launch_status());
+    TRYB(cuda_status(cudaMemsetAsync(xh.v, 0, spinorm_bytes<PV>(lat->g.Vh, N), st)));
+    {
+      ProfScope ps("convert", st);
+      k_mconvert<P, PV, N><<<G, 256, 0, st>>>(p, rh);
+    }
+    TRYB(last_launch_status());
+    pending_p = false;
+    done = (active == 0);
+    return STAG_OK;
+  }
+
+  int iterations(int C) override {
+    const int* flags = &dst->flags;
+    const int Vh = lat->g.Vh;
+    SpinorM<PV> none{nullptr, Vh, N};
+    for (int i = 0; i < C; ++i) {
+      if (pending_p) {
+        ProfScope ps("blas", st);
+        k_mcg_xpay<P, N><<<grid_bw(Vh), 256, 0, st>>>(p, rh, dst);
+        TRYB(last_launch_status());
+      }
+      TRYB((mdslash<P, N>(lat, t, p, 1, flags, st)));
+      TRYB((mdslash_epi<P, N, 1>(lat, Ap, t, 0, p, shift, none, 0.0, -1.0, rs, RedTarget{RED_MCG_ALPHA, dst, nullptr},
+                                 flags, st)));
+      {
+        ProfScope ps("blas", st);
+        k_mcg_update<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(xh, rh, p, Ap, dst,
+                                                                        RedBuf{rs.partials, rs.counter});
+      }
+      TRYB(last_launch_status());
+      pending_p = true;
+    }
+    return STAG_OK;
+  }
+
+  int reliable_update() override {
+    const int Vh = lat->g.Vh;
+    {
+      ProfScope ps("blas", st);
+      k_maccumulate<PV, N><<<grid_bw(Vh), 256, 0, st>>>(y64, xh);
+    }
+    TRYB(last_launch_status());
+    TRYB(true_residual(RedTarget{RED_MCG_RU_RESID, dst, nullptr}));
+    {
+      ProfScope ps("reduce", st);
+      k_mru_convert_dot<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(rh, r64, p, dst,
+                                                                          RedBuf{rs.partials, rs.counter});
+    }
+    TRYB(last_launch_status());
+    {
+      ProfScope ps("blas", st);
+      k_mru_p<P, N><<<grid_bw(Vh), 256, 0, st>>>(p, rh, dst);
+    }
+    TRYB(last_launch_status());
+    pending_p = false;
+    return STAG_OK;
+  }
+
+  int finish() override {
+    {
+      ProfScope ps("convert", st);
+      k_mto_canonical<64, N><<<grid_bw(lat->g.Vh), 256, 0, st>>>(x, y64, nreal);
+    }
+    return last_launch_status();
+  }
+};
+
+template <int P> static std::unique_ptr<GroupBase> make_group(int N) {
+  if (N == 8) return std::unique_ptr<GroupBase>(new Group<P, 8>());
+  if (N == 4) return std::unique_ptr<GroupBase>(new Group<P, 4>());
+  return std::unique_ptr<GroupBase>(new Group<P, 2>());
+}
+
+template <int P>
+static int alloc_group(GroupBase* g, int gid) {
+  const int N = g->n();
+  if (N == 8) return static_cast<Group<P, 8>*>(g)->alloc(gid);
+  if (N == 4) return static_cast<Group<P, 4>*>(g)->alloc(gid);
+  return static_cast<Group<P, 2>*>(g)->alloc(gid);
+}
+
+namespace {
+struct Streams {
+  std::vector<cudaStream_t> s;
+  std::vector<cudaEvent_t> ev;
+  ~Streams() {
+    for (auto x : s) cudaStreamDestroy(x);
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+struct Pinned {
+  void* p = nullptr;
+  ~Pinned() {
+    if (p) cudaFreeHost(p);
+  }
+};
+struct GraphExec {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  ~GraphExec() { reset(); }
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  }
+};
+double now_b() { return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count(); }
+}  // namespace
+
+template <int P>
+static int batch_solve_p(const stag_batch_item* items, int nitems, const stag_solve_params& prm,
+                         stag_solve_info* infos, cudaStream_t origin) {
+  const double t0 = now_b();
+  // groups of 8, 4, 2 right-hand sides per item (a last single one pads to 2)
+  std::vector<std::unique_ptr<GroupBase>> groups;
+  for (int it = 0; it < nitems; ++it) {
+    const stag_batch_item& I = items[it];
+    const size_t n = (size_t)I.lat->g.Vh * 3;
+    int r = 0;
+    while (r < I.nrhs) {
+      const int left = I.nrhs - r;
+      const int N = left >= 8 ? 8 : left >= 4 ? 4 : 2;
+      std::unique_ptr<GroupBase> g = make_group<P>(N);
+      g->lat = I.lat;
+      g->shift = I.mass * I.mass;
+      g->x = (double2*)I.x + r * n;
+      g->b = (const double2*)I.b + r * n;
+      g->nreal = left < N ? left : N;
+      g->item = it;
+      g->first = r;
+      r += g->nreal;
+      groups.push_back(std::move(g));
+    }
+  }
+  const int ng = (int)groups.size();
+  Streams streams;
+  for (int k = 0; k < ng; ++k) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return STAG_ECUDA;
+    }
+    streams.s.push_back(s);
+    groups[k]->st = s;
+  }
+  for (int k = 0; k < 2 * ng + 2; ++k) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return STAG_ECUDA;
+    }
+    streams.ev.push_back(e);
+  }
+  Pinned pin;
+  const size_t per = sizeof(McgState) + sizeof(double) * 2 * MAX_RHS;
+  if (cudaMallocHost(&pin.p, per * ng) != cudaSuccess) {
+    cudaGetLastError();
+    return STAG_ENOMEM;
+  }
+  for (int k = 0; k < ng; ++k) {
+    groups[k]->hst = (McgState*)((char*)pin.p + per * k);
+    groups[k]->hscal = (double*)((char*)pin.p + per * k + sizeof(McgState));
+    TRYB(alloc_group<P>(groups[k].get(), k));
+  }
+  // fork: the group streams start after the work already queued on `origin`
+  TRYB(cuda_status(cudaEventRecord(streams.ev[0], origin)));
+  for (int k = 0; k < ng; ++k) TRYB(cuda_status(cudaStreamWaitEvent(groups[k]->st, streams.ev[0], 0)));
+  for (auto& g : groups) TRYB(g->setup(prm));
+  for (auto& g : groups) TRYB(cuda_status(cudaStreamSynchronize(g->st)));
+  for (auto& g : groups) TRYB(g->start(prm));
+
+  const int C = prm.check_interval > 0 ? prm.check_interval : 16;
+  GraphExec graph;
+  std::vector<int> graph_set;  // groups captured in the current graph
+  long long graph_kernels = 0;  // kernels per replay
+  cudaStream_t cap = nullptr;   // capture / launch stream of the graph
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return STAG_ECUDA;
+  }
+  streams.s.push_back(cap);
+  long long chunks = 0, max_chunks = (long long)prm.max_iter / C + 64 * ng + 64;
+  for (;;) {
+    std::vector<int> live;
+    for (int k = 0; k < ng; ++k)
+      if (!groups[k]->done) live.push_back(k);
+    if (live.empty()) break;
+    if (++chunks > max_chunks) {
+      for (int k : live) groups[k]->status = STAG_ENOTCONV, groups[k]->done = true;
+      break;
+    }
+    bool steady = true;  // every live group begins with its direction update
+    for (int k : live) steady = steady && groups[k]->pending_p;
+    if (!steady) {
+      // first chunk after a start or a reliable update: queue directly
+      for (int k : live) TRYB(groups[k]->iterations(C));
+      for (int k : live) TRYB(cuda_status(cudaStreamSynchronize(groups[k]->st)));
+    } else {
+      if (graph_set != live || graph.exec == nullptr) {
+        // capture one chunk of every live group: cap forks to the group
+        // streams and joins back; recorded, not run
+        graph.reset();
+        graph_set.clear();
+        set_capturing(true);
+        int s = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        if (!s) s = cuda_status(cudaEventRecord(streams.ev[1], cap));
+        for (size_t j = 0; j < live.size() && !s; ++j) s = cuda_status(cudaStreamWaitEvent(groups[live[j]]->st, streams.ev[1], 0));
+        for (size_t j = 0; j < live.size() && !s; ++j) s = groups[live[j]]->iterations(C);
+        for (size_t j = 0; j < live.size() && !s; ++j) {
+          s = cuda_status(cudaEventRecord(streams.ev[2 + j], groups[live[j]]->st));
+          if (!s) s = cuda_status(cudaStreamWaitEvent(cap, streams.ev[2 + j], 0));
+        }
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cap, &gr);
+        graph_kernels = set_capturing(false);
+        if (s || e != cudaSuccess || gr == nullptr) {
+          cudaGetLastError();
+          if (gr) cudaGraphDestroy(gr);
+          return s ? s : STAG_ECUDA;
+        }
+        graph.graph = gr;
+        if (cudaGraphInstantiate(&graph.exec, gr, 0) != cudaSuccess) {
+          cudaGetLastError();
+          graph.reset();
+          return STAG_ECUDA;
+        }
+        graph_set = live;
+      }
+      TRYB(cuda_status(cudaGraphLaunch(graph.exec, cap)));
+      for (long long i = 0; i < graph_kernels; ++i) count_launch();
+      TRYB(cuda_status(cudaStreamSynchronize(cap)));
+    }
+    // read every live group's state
+    for (int k : live) {
+      GroupBase& g = *groups[k];
+      TRYB(cuda_status(cudaMemcpyAsync(g.hst, g.dst, sizeof(McgState), cudaMemcpyDeviceToHost, g.st)));
+    }
+    for (int k : live) TRYB(cuda_status(cudaStreamSynchronize(groups[k]->st)));
+    prof_flush_completed();
+    std::vector<int> ru;
+    for (int k : live) {
+      GroupBase& g = *groups[k];
+      if (g.hst->flags & F_BREAKDOWN) {
+        g.status = STAG_EBREAKDOWN;
+        g.done = true;
+      } else if (g.hst->flags & (F_CONVERGED | F_NEED_RU | F_ITER_CAP)) {
+        ru.push_back(k);
+      }
+    }
+    for (int k : ru) TRYB(groups[k]->reliable_update());
+    for (int k : ru) {
+      GroupBase& g = *groups[k];
+      TRYB(cuda_status(cudaMemcpyAsync(g.hst, g.dst, sizeof(McgState), cudaMemcpyDeviceToHost, g.st)));
+    }
+    for (int k : ru) {
+      GroupBase& g = *groups[k];
+      TRYB(cuda_status(cudaStreamSynchronize(g.st)));
+      if (g.hst->flags & F_BREAKDOWN) {
+        g.status = STAG_EBREAKDOWN;
+        g.done = true;
+      } else if (g.hst->active == 0) {
+        g.done = true;
+      } else if (g.hst->iter >= prm.max_iter) {
+        g.status = STAG_ENOTCONV;
+        g.done = true;
+      }
+    }
+  }
+  for (auto& g : groups) TRYB(g->finish());
+  // join: `origin` continues after every group's last kernel
+  for (int k = 0; k < ng; ++k) {
+    TRYB(cuda_status(cudaEventRecord(streams.ev[2 + k], groups[k]->st)));
+    TRYB(cuda_status(cudaStreamWaitEvent(origin, streams.ev[2 + k], 0)));
+  }
+  TRYB(cuda_status(cudaStreamSynchronize(origin)));
+  const double t1 = now_b();
+  int worst = STAG_OK;
+  for (auto& g : groups) {
+    if (g->status && !worst) worst = g->status;
+    if (!infos) continue;
+    // info order: item by item, right-hand side by right-hand side
+    int off = 0;
+    for (int it = 0; it < g->item; ++it) off += items[it].nrhs;
+    for (int i = 0; i < g->nreal; ++i) {
+      stag_solve_info& inf = infos[off + g->first + i];
+      const CgState& c = g->hst->sys[i];
+      inf.iters = c.iter;
+      inf.reliable_updates = g->hst->reliable_updates;
+      inf.true_rel_resid = g->bb[i] > 0.0 ? std::sqrt(c.rr_true / g->bb[i]) : 0.0;
+      inf.converged = g->bb[i] > 0.0 ? (c.rr_true <= c.target) : 1;
+      inf.status = g->status ? g->status : (inf.converged ? STAG_OK : STAG_ENOTCONV);
+      inf.seconds = t1 - t0;
+      if (!inf.converged && !worst) worst = STAG_ENOTCONV;
+    }
+  }
+  return worst;
+}
+
+}  // namespace stag
+
+using namespace stag;
+
+extern "C" int stag_batch_solve(const stag_batch_item* items, int nitems, const stag_solve_params* params,
+                                stag_solve_info* infos, void* stream) {
+  if (!items || nitems <= 0) return STAG_EINVAL;
+  stag_solve_params prm;
+  stag_default_params(&prm);
+  if (params) prm = *params;
+  if (!(prm.tol > 0.0) || prm.max_iter < 0 || prm.mode < 0 || prm.mode > 3) return STAG_EINVAL;
+  if (prm.mode != STAG_PLAIN64 && !(prm.delta > 0.0 && prm.delta < 1.0)) return STAG_EINVAL;
+  const int pi = prm.mode == STAG_PLAIN64 ? STAG_FP64 : prm.mode == STAG_MIXED32 ? STAG_FP32
+               : prm.mode == STAG_MIXED16 ? STAG_FP16 : STAG_FX16;
+  for (int i = 0; i < nitems; ++i) {
+    const stag_batch_item& I = items[i];
+    if (!I.lat || !I.x || !I.b || I.nrhs <= 0) return STAG_EINVAL;
+    if (!I.lat->links[STAG_FP64].present || !I.lat->links[pi].present) return STAG_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (prm.mode) {
+    case STAG_PLAIN64: return batch_solve_p<64>(items, nitems, prm, infos, st);
+    case STAG_MIXED32: return batch_solve_p<32>(items, nitems, prm, infos, st);
+    case STAG_MIXED16: return batch_solve_p<16>(items, nitems, prm, infos, st);
+    default: return batch_solve_p<15>(items, nitems, prm, infos, st);
+  }
+}

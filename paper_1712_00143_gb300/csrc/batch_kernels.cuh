@@ -1,0 +1,313 @@
+// batch_kernels.cuh -- kernels of the multi-right-hand-side CG: the N-RHS
+// Dslash (plain and with the fused axpy and per-system FP64 reductions) and
+// the per-system level-1 kernels, all on the MRHS layout of dslash_mrhs.cuh.
+// Each system i of a group reads its own scalars (alpha_i, beta_i ...) from
+// the group's McgState.
+#pragma once
+#include "dslash_mrhs.cuh"
+
+namespace stag {
+
+constexpr int MB = 128;  // threads per block of the N-RHS kernels
+
+template <int P, int NL, int N>
+__global__ void __launch_bounds__(MB) k_dslash_m(DslashArgsM<P> a, SpinorM<P> out, const int* flags) {
+  if (stopped(flags)) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.g.Vh) return;
+  typename Prec<P>::A2 d[N][3];
+  dslash_site_m<P, NL, N>(a, s, d);
+#pragma unroll
+  for (int r = 0; r < N; ++r) SpinorLoadM<P>::st(out, s, r, d[r]);
+}
+
+// out_r = ax x_r + ay y_r + ad (D in)_r; RED = 1: Re<x_r, out_r>, RED = 2:
+// ||out_r||^2, one FP64 sum per system, finalised by the last block.
+template <int P, int NL, int N, int RED>
+__global__ void __launch_bounds__(MB)
+    k_dslash_m_epi(DslashArgsM<P> a, SpinorM<Acc<P>::value> out, SpinorM<P> x, double ax,
+                   SpinorM<Acc<P>::value> y, double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags) {
+  using A2 = typename Prec<P>::A2;
+  using A = typename Prec<P>::A;
+  constexpr int PA = Acc<P>::value;
+  if (stopped(flags)) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  double red[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) red[r] = 0.0;
+  if (s < a.g.Vh) {
+    A2 d[N][3];
+    dslash_site_m<P, NL, N>(a, s, d);
+    const A cx = (A)ax, cd = (A)ad, cy = (A)ay;
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      A2 xv[3], o[3];
+      SpinorLoadM<P>::ld(x, s, r, xv);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        o[i].x = cx * xv[i].x + cd * d[r][i].x;
+        o[i].y = cx * xv[i].y + cd * d[r][i].y;
+      }
+      if (ay != 0.0) {
+        A2 yv[3];
+        SpinorLoadM<PA>::ld(y, s, r, yv);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          o[i].x += cy * yv[i].x;
+          o[i].y += cy * yv[i].y;
+        }
+      }
+      SpinorLoadM<PA>::st(out, s, r, o);
+      if (RED) {
+        Acc1<A> acc;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          acc.add_prod(RED == 1 ? xv[i].x : o[i].x, o[i].x);
+          acc.add_prod(RED == 1 ? xv[i].y : o[i].y, o[i].y);
+        }
+        red[r] = acc.value();
+      }
+    }
+  }
+  if (RED) grid_reduce<N>(red, rb, tgt);
+}
+
+// ------------------------------------------------------------ level 1
+// grid-stride over sites, all N systems of a site per trip
+#define MGRID(s, Vh) for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < (Vh); s += gridDim.x * blockDim.x)
+
+// xh_r += alpha_r p_r; rh_r -= alpha_r Ap_r; ||rh_r||^2 -> RED_MCG_BETA
+template <int P, int N>
+__global__ void __launch_bounds__(256) k_mcg_update(SpinorM<Acc<P>::value> xh, SpinorM<Acc<P>::value> rh,
+                                                     SpinorM<P> p, SpinorM<Acc<P>::value> Ap, McgState* g,
+                                                     RedBuf rb) {
+  constexpr int PV = Acc<P>::value;
+  using A2 = typename Prec<PV>::A2;
+  using A = typename Prec<PV>::A;
+  if (stopped(&g->flags)) return;
+  A alpha[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) alpha[r] = (A)__ldcg(&g->sys[r].alpha);
+  Acc1<A> acc[N];
+  MGRID(s, xh.Vh) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      A2 x[3], rv[3], ap[3];
+      typename Prec<P>::A2 pv[3];
+      SpinorLoadM<PV>::ldw(xh, s, r, x);
+      SpinorLoadM<PV>::ldw(rh, s, r, rv);
+      SpinorLoadM<P>::ld(p, s, r, pv);
+      SpinorLoadM<PV>::ld(Ap, s, r, ap);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        x[c].x += alpha[r] * (A)pv[c].x;
+        x[c].y += alpha[r] * (A)pv[c].y;
+        rv[c].x -= alpha[r] * ap[c].x;
+        rv[c].y -= alpha[r] * ap[c].y;
+        acc[r].add_prod(rv[c].x, rv[c].x);
+        acc[r].add_prod(rv[c].y, rv[c].y);
+      }
+      SpinorLoadM<PV>::st(xh, s, r, x);
+      SpinorLoadM<PV>::st(rh, s, r, rv);
+    }
+  }
+  double red[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) red[r] = acc[r].value();
+  grid_reduce<N>(red, rb, RedTarget{RED_MCG_BETA, g, nullptr});
+}
+
+// p_r = rh_r + beta_r p_r
+template <int P, int N>
+__global__ void __launch_bounds__(256) k_mcg_xpay(SpinorM<P> p, SpinorM<Acc<P>::value> rh, McgState* g) {
+  using A2 = typename Prec<P>::A2;
+  using A = typename Prec<P>::A;
+  if (stopped(&g->flags)) return;
+  A beta[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) beta[r] = (A)__ldcg(&g->sys[r].beta);
+  MGRID(s, p.Vh) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      A2 pv[3];
+      typename Prec<Acc<P>::value>::A2 rv[3];
+      SpinorLoadM<P>::ldw(p, s, r, pv);
+      SpinorLoadM<Acc<P>::value>::ld(rh, s, r, rv);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pv[c].x = (A)rv[c].x + beta[r] * pv[c].x;
+        pv[c].y = (A)rv[c].y + beta[r] * pv[c].y;
+      }
+      SpinorLoadM<P>::st(p, s, r, pv);
+    }
+  }
+}
+
+// y_r += xh_r; xh_r = 0
+template <int PV, int N> __global__ void k_maccumulate(SpinorM<64> y, SpinorM<PV> xh) {
+  MGRID(s, y.Vh) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      double2 a[3];
+      typename Prec<PV>::A2 b[3], z[3];
+      SpinorLoadM<64>::ldw(y, s, r, a);
+      SpinorLoadM<PV>::ldw(xh, s, r, b);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        a[c].x += (double)b[c].x;
+        a[c].y += (double)b[c].y;
+        z[c].x = 0;
+        z[c].y = 0;
+      }
+      SpinorLoadM<64>::st(y, s, r, a);
+      SpinorLoadM<PV>::st(xh, s, r, z);
+    }
+  }
+}
+
+// rh_r = r64_r (rounded); <rh_r, p_r> -> RED_MCG_RU_ORTHO (2N values)
+template <int P, int N>
+__global__ void k_mru_convert_dot(SpinorM<Acc<P>::value> rh, SpinorM<64> r64, SpinorM<P> p, McgState* g, RedBuf rb) {
+  constexpr int PV = Acc<P>::value;
+  using A2 = typename Prec<PV>::A2;
+  using A = typename Prec<PV>::A;
+  Acc1<A> re[N], im[N];
+  MGRID(s, r64.Vh) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      double2 a[3];
+      A2 o[3];
+      typename Prec<P>::A2 pv[3];
+      SpinorLoadM<64>::ld(r64, s, r, a);
+      SpinorLoadM<P>::ld(p, s, r, pv);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        o[c].x = a[c].x;
+        o[c].y = a[c].y;
+      }
+      SpinorLoadM<PV>::st(rh, s, r, o);
+      SpinorLoadM<PV>::ldw(rh, s, r, o);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        re[r].add_prod(o[c].x, (A)pv[c].x);
+        re[r].add_prod(o[c].y, (A)pv[c].y);
+        im[r].add_prod(o[c].x, (A)pv[c].y);
+        im[r].add_prod(-o[c].y, (A)pv[c].x);
+      }
+    }
+  }
+  double red[2 * N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    red[2 * r] = re[r].value();
+    red[2 * r + 1] = im[r].value();
+  }
+  grid_reduce<2 * N>(red, rb, RedTarget{RED_MCG_RU_ORTHO, g, nullptr});
+}
+
+// p_r = rh_r + beta_r (p_r - c_r rh_r)
+template <int P, int N> __global__ void k_mru_p(SpinorM<P> p, SpinorM<Acc<P>::value> rh, McgState* g) {
+  using A2 = typename Prec<P>::A2;
+  using A = typename Prec<P>::A;
+  A beta[N], cr[N], ci[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    beta[r] = (A)__ldcg(&g->sys[r].beta);
+    cr[r] = (A)__ldcg(&g->sys[r].ortho_re);
+    ci[r] = (A)__ldcg(&g->sys[r].ortho_im);
+  }
+  MGRID(s, p.Vh) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      A2 pv[3];
+      typename Prec<Acc<P>::value>::A2 rv[3];
+      SpinorLoadM<P>::ldw(p, s, r, pv);
+      SpinorLoadM<Acc<P>::value>::ld(rh, s, r, rv);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        A rx = (A)rv[c].x, ry = (A)rv[c].y;
+        A qx = pv[c].x - (cr[r] * rx - ci[r] * ry);
+        A qy = pv[c].y - (cr[r] * ry + ci[r] * rx);
+        pv[c].x = rx + beta[r] * qx;
+        pv[c].y = ry + beta[r] * qy;
+      }
+      SpinorLoadM<P>::st(p, s, r, pv);
+    }
+  }
+}
+
+// MRHS out (systems 0..N-1) <- canonical in[r] for r < nreal, zero for the rest
+template <int P, int N> __global__ void k_mfrom_canonical(SpinorM<P> out, const double2* __restrict__ in, int nreal) {
+  using A2 = typename Prec<P>::A2;
+  MGRID(s, out.Vh) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      A2 o[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double2 v = r < nreal ? in[((size_t)r * out.Vh + s) * 3 + c] : make_double2(0.0, 0.0);
+        o[c].x = v.x;
+        o[c].y = v.y;
+      }
+      SpinorLoadM<P>::st(out, s, r, o);
+    }
+  }
+}
+
+// canonical out[r] <- MRHS in, r < nreal
+template <int P, int N> __global__ void k_mto_canonical(double2* __restrict__ out, SpinorM<P> in, int nreal) {
+  using A2 = typename Prec<P>::A2;
+  MGRID(s, in.Vh) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      if (r >= nreal) break;
+      A2 o[3];
+      SpinorLoadM<P>::ld(in, s, r, o);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[((size_t)r * in.Vh + s) * 3 + c] = make_double2((double)o[c].x, (double)o[c].y);
+    }
+  }
+}
+
+template <int PO, int PI, int N> __global__ void k_mconvert(SpinorM<PO> out, SpinorM<PI> in) {
+  MGRID(s, in.Vh) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      typename Prec<PI>::A2 a[3];
+      typename Prec<PO>::A2 o[3];
+      SpinorLoadM<PI>::ld(in, s, r, a);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        o[c].x = a[c].x;
+        o[c].y = a[c].y;
+      }
+      SpinorLoadM<PO>::st(out, s, r, o);
+    }
+  }
+}
+
+// ||v_r||^2 for every system -> RED_STORE (N values)
+template <int P, int N> __global__ void k_mnorm2(SpinorM<P> v, RedBuf rb, RedTarget tgt) {
+  using A = typename Prec<P>::A;
+  Acc1<A> acc[N];
+  MGRID(s, v.Vh) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      typename Prec<P>::A2 a[3];
+      SpinorLoadM<P>::ld(v, s, r, a);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[r].add_prod(a[c].x, a[c].x);
+        acc[r].add_prod(a[c].y, a[c].y);
+      }
+    }
+  }
+  double red[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) red[r] = acc[r].value();
+  grid_reduce<N>(red, rb, tgt);
+}
+
+#undef MGRID
+
+}  // namespace stag

@@ -323,6 +323,21 @@ struct MsState {
   int iters[MAX_SHIFTS];
 };
 
+constexpr int MAX_RHS = 8;
+// Scalars of a group of up to MAX_RHS CG systems that share one lattice (and
+// one multi-right-hand-side Dslash): per-system recurrences plus group flags.
+// A system whose iterated residual reaches its target leaves the active set
+// (its alpha and beta become 0, so its vectors stop changing); the group stops
+// for a reliable update when any active system triggers one.
+struct McgState {
+  int n;
+  int active;  // bit i: system i still iterates
+  int flags;   // group flags (F_*): CONVERGED = no active system left
+  int iter, max_iter;
+  int reliable_updates;
+  CgState sys[MAX_RHS];
+};
+
 enum RedOp : int {
   RED_STORE = 0,      // out[0..NV) = totals
   RED_CG_ALPHA = 1,   // pAp -> alpha
@@ -331,6 +346,10 @@ enum RedOp : int {
   RED_RU_ORTHO = 4,   // <r,p> (re, im) -> ortho coefficient
   RED_MS_ALPHA = 5,   // base pAp -> alpha and per-shift zeta, alpha_s
   RED_MS_BETA = 6,    // ||r||^2 -> beta, per-shift beta_s, shift stopping
+  RED_MCG_ALPHA = 7,  // per-system pAp -> alpha (McgState)
+  RED_MCG_BETA = 8,   // per-system ||r||^2 -> beta, activity, group flags
+  RED_MCG_RU_RESID = 9,  // per-system true ||r||^2 after a reliable update
+  RED_MCG_RU_ORTHO = 10, // per-system <r,p> (re, im pairs)
 };
 
 struct RedTarget {
@@ -456,6 +475,85 @@ __device__ inline void finalize(const RedTarget& t, const double* v, int nv) {
       ms->stop_mask = stop;
       if ((mask & ~stop) == 0) st->flags |= F_CONVERGED;
       if (st->iter >= st->max_iter) st->flags |= F_ITER_CAP;
+      break;
+    }
+    case RED_MCG_ALPHA: {
+      McgState* g = (McgState*)t.state;
+      for (int i = 0; i < g->n; ++i) {
+        CgState* st = &g->sys[i];
+        if (!((g->active >> i) & 1)) {
+          st->alpha = 0.0;
+          continue;
+        }
+        st->pAp = v[i];
+        if (!(v[i] > 0.0) || !finite_d(v[i])) {
+          st->flags |= F_BREAKDOWN;
+          g->flags |= F_BREAKDOWN;
+        } else {
+          st->alpha = st->rr / v[i];
+        }
+      }
+      break;
+    }
+    case RED_MCG_BETA: {
+      McgState* g = (McgState*)t.state;
+      g->iter += 1;
+      int active = g->active;
+      for (int i = 0; i < g->n; ++i) {
+        CgState* st = &g->sys[i];
+        if (!((active >> i) & 1)) {
+          st->beta = 0.0;
+          continue;
+        }
+        const double rr_new = v[i];
+        if (!finite_d(rr_new)) {
+          st->flags |= F_BREAKDOWN;
+          g->flags |= F_BREAKDOWN;
+          continue;
+        }
+        st->beta = rr_new / st->rr;
+        st->rr_prev = st->rr;
+        st->rr = rr_new;
+        st->iter = g->iter;
+        if (rr_new > st->rr_max) st->rr_max = rr_new;
+        if (rr_new <= st->target) active &= ~(1 << i);
+        if (st->delta2 > 0.0 && rr_new < st->delta2 * st->rr_max) g->flags |= F_NEED_RU;
+      }
+      g->active = active;
+      if (active == 0) g->flags |= F_CONVERGED;
+      if (g->iter >= g->max_iter) g->flags |= F_ITER_CAP;
+      break;
+    }
+    case RED_MCG_RU_RESID: {
+      McgState* g = (McgState*)t.state;
+      int active = 0;
+      for (int i = 0; i < g->n; ++i) {
+        CgState* st = &g->sys[i];
+        const double rr = v[i];
+        st->rr_true = rr;
+        if (!finite_d(rr)) {
+          g->flags |= F_BREAKDOWN;
+          continue;
+        }
+        st->beta = st->rr_prev > 0.0 ? rr / st->rr_prev : 0.0;
+        st->rr = rr;
+        st->rr_max = rr;
+        if (rr > st->target) active |= 1 << i;
+      }
+      g->active = active;
+      g->reliable_updates += 1;
+      g->flags &= ~(F_CONVERGED | F_NEED_RU);
+      if (active == 0) g->flags |= F_CONVERGED;
+      break;
+    }
+    case RED_MCG_RU_ORTHO: {
+      McgState* g = (McgState*)t.state;
+      for (int i = 0; i < g->n; ++i) {
+        CgState* st = &g->sys[i];
+        st->ortho_re = st->rr > 0.0 ? v[2 * i] / st->rr : 0.0;
+        st->ortho_im = st->rr > 0.0 ? v[2 * i + 1] / st->rr : 0.0;
+        if (!((g->active >> i) & 1)) st->beta = 0.0;
+      }
       break;
     }
   }

@@ -57,6 +57,12 @@ void prof_begin(const char* family, cudaStream_t s);
 void prof_end(cudaStream_t s);
 void prof_flush_completed();
 void count_launch();
+// While capturing a CUDA graph: no profiling events, and kernel launches are
+// counted aside; set_capturing(false) returns how many were captured.
+long long set_capturing(bool on);
+// stag_dslash for nrhs > 1 (N-right-hand-side kernels)
+int dslash_multi(stag_lattice_s* lat, double2* out, const double2* in, int out_parity, int prec, int nrhs,
+                 cudaStream_t st);
 
 struct ProfScope {
   cudaStream_t s;
@@ -70,13 +76,13 @@ struct ProfScope {
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? STAG_OK : STAG_ECUDA; }
 int last_launch_status();
 
-// Reduction scratch: [2][max_grid] partial sums and a ticket counter.
+// Reduction scratch: [nv_max][max_grid] partial sums and a ticket counter.
 struct RedScratch {
   double* partials;
   unsigned* counter;
   int max_grid;
 };
-int get_red_scratch(stag_lattice_s* lat, const char* name, RedScratch* out);
+int get_red_scratch(stag_lattice_s* lat, const char* name, RedScratch* out, int nv_max = 2);
 
 // A Spinor<P> living in the handle's workspace buffer `name`.
 template <int P> Spinor<P> ws_spinor(stag_lattice_s* lat, const std::string& name, int* status);

@@ -1,0 +1,113 @@
+"""Batched solves (many right-hand sides on several lattices in one call):
+every system must reach 1e-10 FP64 true residual, recomputed by the oracle
+(whole field on small lattices, sampled sites on the full-size workload)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_common import Field, dev, rel_l2, requires_gpu
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+
+def _stag():
+    import paper_1712_00143_gb300 as stag
+
+    return stag
+
+
+@pytest.mark.parametrize("mode", ["plain64", "mixed32", "mixedfx16", "mixed16"])
+def test_batch_small_two_lattices(mode):
+    stag = _stag()
+    specs = [((8, 8, 8, 8), 0.1, 3, 1000), ((4, 6, 8, 10), 0.05, 8, 1001), ((4, 4, 4, 6), 0.2, 1, 1002)]
+    fields, handles, items, bs, xs = [], [], [], [], []
+    for dims, mass, nrhs, seed in specs:
+        fat, lng = synth.gauge_field(dims, 0.3, seed)
+        h = stag.stag_load_links(dims, dev(fat), dev(lng), recon_long=12)
+        b = synth.gaussian_source(dims, 5000 + seed, nrhs=nrhs)
+        bd = dev(b)
+        x = torch.zeros_like(bd)
+        fields.append((dims, fat, lng, mass))
+        handles.append(h)
+        bs.append(b)
+        xs.append(x)
+        items.append((h, x, bd, nrhs, mass))
+    infos = stag.stag_batch_solve(items, mode=mode, tol=1e-10)
+    k = 0
+    for (dims, fat, lng, mass), b, x in zip(fields, bs, xs):
+        xh = x.cpu().numpy()
+        for i in range(b.shape[0]):
+            res = oracle.true_residual(fat, lng, xh[i], b[i], mass, dims)
+            assert infos[k]["converged"] and res <= 1e-10, (mode, dims, i, infos[k], res)
+            assert abs(infos[k]["true_rel_resid"] - res) < 1e-11
+            k += 1
+    # a batched system takes about as many iterations as the same system alone
+    h, x, bd, nrhs, mass = items[0]
+    xs1 = torch.zeros_like(bd[0])
+    single = stag.stag_cg(h, xs1, bd[0].contiguous(), mass, mode=mode, tol=1e-10)
+    assert abs(infos[0]["iters"] - single["iters"]) <= 0.1 * single["iters"] + 16
+    for h in handles:
+        h.free()
+
+
+def test_batch_initial_guess_and_zero_rhs():
+    stag = _stag()
+    dims = (4, 6, 8, 10)
+    f = Field.get(dims)
+    h = f.handle(recon=12)
+    b = synth.gaussian_source(dims, 77, nrhs=4)
+    b[2] = 0.0  # a zero right-hand side is solved by x = 0
+    xo = [oracle.cg(f.fat, f.lng, b[i], 0.05, dims, tol=1e-12)[0] if i != 2 else 0.0 * b[i] for i in range(4)]
+    x0 = np.stack([xo[i] + 1e-5 * synth.random_spinor(dims, 90 + i) for i in range(4)])
+    x0[2] = 0.0
+    x = dev(x0)
+    infos = stag.stag_batch_solve([(h, x, dev(b), 4, 0.05)], mode="mixed32", tol=1e-10, use_initial_guess=1)
+    xh = x.cpu().numpy()
+    for i in range(4):
+        assert infos[i]["converged"]
+        if i == 2:
+            assert np.abs(xh[i]).max() == 0.0
+        else:
+            assert oracle.true_residual(f.fat, f.lng, xh[i], b[i], 0.05, dims) <= 1e-10
+    h.free()
+
+
+def test_batch_full_workload_12_lattices():
+    """4 x 16^4 + 4 x 24^3x48 + 4 x 32^4, 8 Gaussian right-hand sides each,
+    m cycling over 0.01, 0.02, 0.05, mixed FP32 with FP64 reliable updates."""
+    stag = _stag()
+    dims_list = [(16, 16, 16, 16)] * 4 + [(24, 24, 24, 48)] * 4 + [(32, 32, 32, 32)] * 4
+    masses = [0.01, 0.02, 0.05]
+    rng = np.random.default_rng(3)
+    items, keep = [], []
+    for j, dims in enumerate(dims_list):
+        fat, lng = synth.gauge_field(dims, 0.3, 1000 + j)
+        h = stag.stag_load_links(dims, dev(fat), dev(lng), recon_long=12, prec_mask=0b0011)
+        b = synth.gaussian_source(dims, 5000 + 100 * j, nrhs=8)
+        bd = dev(b)
+        x = torch.zeros_like(bd)
+        mass = masses[j % 3]
+        items.append((h, x, bd, 8, mass))
+        keep.append((dims, fat, lng, mass, b, x, h))
+    torch.cuda.synchronize()
+    import time
+
+    t = time.time()
+    infos = stag.stag_batch_solve(items, mode="mixed32", tol=1e-10)
+    el = time.time() - t
+    assert len(infos) == 96
+    k = 0
+    for dims, fat, lng, mass, b, x, h in keep:
+        xh = x.cpu().numpy()
+        sites = np.unique(rng.integers(0, b.shape[1], 500))
+        for i in range(8):
+            assert infos[k]["converged"] and infos[k]["true_rel_resid"] <= 1e-10, (dims, i, infos[k])
+            mx = oracle.apply_m_at_sites(fat, lng, xh[i], mass, dims, sites)
+            r = b[i][sites] - mx
+            assert np.linalg.norm(r) / np.linalg.norm(b[i][sites]) < 3e-10
+            k += 1
+        h.free()
+    print(f"batched 96 systems on 12 lattices: {el:.3f} s")

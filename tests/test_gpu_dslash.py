@@ -49,18 +49,21 @@ def test_dslash_all_precisions(dims, recon):
     h.free()
 
 
-def test_dslash_multiple_rhs():
+@pytest.mark.parametrize("nrhs", [2, 3, 8, 11])
+def test_dslash_multiple_rhs(nrhs):
+    """N-right-hand-side kernel (groups of 8, 4, 2 plus a single one) in every format."""
     stag = _stag()
     dims = (4, 6, 8, 10)
     f = Field.get(dims)
-    h = f.handle()
-    nrhs = 3
+    h = f.handle(recon=12)
     psi = np.stack([synth.random_spinor(dims, 20 + k) for k in range(nrhs)])
-    out = torch.empty(psi.shape, dtype=torch.complex128, device="cuda")
-    stag.stag_dslash(h, out, dev(psi), 1, "fp32", nrhs=nrhs)
-    got = out.cpu().numpy()
-    for k in range(nrhs):
-        assert rel_l2(got[k], oracle.dslash(f.fat, f.lng, psi[k], dims, 1)) < 1e-6
+    refs = [oracle.dslash(f.fat, f.lng, psi[k], dims, 1) for k in range(nrhs)]
+    for prec, tol in TOL_DSLASH.items():
+        out = torch.empty(psi.shape, dtype=torch.complex128, device="cuda")
+        stag.stag_dslash(h, out, dev(psi), 1, prec, nrhs=nrhs)
+        got = out.cpu().numpy()
+        for k in range(nrhs):
+            assert rel_l2(got[k], refs[k]) < tol, (prec, nrhs, k)
     h.free()
 
 
