@@ -440,32 +440,135 @@ def run_dslash_sweep(args):
         fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
         fd, ld = torch.from_numpy(fat).cuda(), torch.from_numpy(lng).cuda()
         del fat, lng
-        psi = torch.from_numpy(synth.random_spinor(dims, 3)).cuda()
-        out = torch.empty_like(psi)
         for recon in args.sweep_recons:
             for prec in args.sweep_precs:
                 if prec == "fp64" and recon == 12:
                     continue
                 h = stag.stag_load_links(dims, fd, ld, recon_long=recon, prec_mask=1 << stag.PREC[prec])
-                for _ in range(3):
-                    stag.stag_dslash(h, out, psi, 1, prec)
-                torch.cuda.synchronize()
-                stag.stag_profile_reset()
-                stag.stag_profile_enable(True)
-                for _ in range(args.sweep_reps):
-                    stag.stag_dslash(h, out, psi, 1, prec)
-                n, ms = stag.stag_profile_read("dslash")
-                stag.stag_profile_enable(False)
-                per = ms / max(n, 1)
-                byt = dslash_bytes_per_site(prec, recon) * h.Vh
-                gbs = byt / (per * 1e-3) / 1e9
-                print(json.dumps({"dslash": "x".join(map(str, dims)), "prec": prec, "recon": recon,
-                                  "us": per * 1e3, "GB/s": gbs, "frac": gbs / peak, "peak_kind": peak_kind,
-                                  "GFLOP/s": FLOP_PER_SITE * h.Vh / (per * 1e-3) / 1e9,
-                                  "bytes_per_launch": byt}), flush=True)
+                for nrhs in args.sweep_nrhs:
+                    psi = torch.from_numpy(synth.random_spinor(dims, 3)).cuda()
+                    if nrhs > 1:
+                        psi = psi.unsqueeze(0).repeat(nrhs, 1, 1).contiguous()
+                    out = torch.empty_like(psi)
+                    fam = "dslash" if nrhs == 1 else "dslash_mrhs"
+                    for _ in range(3):
+                        stag.stag_dslash(h, out, psi, 1, prec, nrhs=nrhs)
+                    torch.cuda.synchronize()
+                    stag.stag_profile_reset()
+                    stag.stag_profile_select(fam, 1)
+                    stag.stag_profile_enable(True)
+                    for _ in range(args.sweep_reps):
+                        stag.stag_dslash(h, out, psi, 1, prec, nrhs=nrhs)
+                    n, ms = stag.stag_profile_read(fam)
+                    stag.stag_profile_enable(False)
+                    stag.stag_profile_select("", 1)
+                    per = ms / max(n, 1)  # one launch covers min(nrhs, 8) right-hand sides
+                    k = nrhs if nrhs <= 8 else 8
+                    nl = 6 if (recon == 12 and prec != "fp64") else 9
+                    byt = ((8 * 9 + 8 * nl) * ELEM_BYTES[prec] + 2 * k * VEC_BYTES[prec]) * h.Vh
+                    gbs = byt / (per * 1e-3) / 1e9
+                    print(json.dumps({"dslash": "x".join(map(str, dims)), "prec": prec, "recon": recon, "nrhs": k,
+                                      "us": per * 1e3, "GB/s": gbs, "frac": gbs / peak, "peak_kind": peak_kind,
+                                      "GFLOP/s": FLOP_PER_SITE * k * h.Vh / (per * 1e-3) / 1e9,
+                                      "us_per_rhs": per * 1e3 / k, "bytes_per_launch": byt}), flush=True)
+                    del psi, out
                 h.free()
-        del fd, ld, psi, out
+        del fd, ld
         torch.cuda.empty_cache()
+
+
+def _timed(fn, reps=1):
+    import torch
+
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    out = None
+    for _ in range(reps):
+        out = fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t) / reps, out
+
+
+def run_config(args):
+    """Secondary workloads of the paper's CG path, one JSON line each (not the
+    headline): `small` 8^4 FP64 CG; `multishift` 48^3x96 nine-shift CG;
+    `batch` 12 lattices x 8 right-hand sides in one batched call vs one
+    stag_cg per system."""
+    import torch
+
+    import paper_1712_00143_gb300 as stag
+    import synth
+
+    dev = torch.device("cuda")
+    if args.config == "small":
+        dims, mass = (8, 8, 8, 8), 0.1
+        fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
+        h = stag.stag_load_links(dims, torch.from_numpy(fat).to(dev), torch.from_numpy(lng).to(dev))
+        b = torch.from_numpy(synth.gaussian_source(dims, 5000)).to(dev)
+        res = {}
+        for mode in ("plain64", "mixed32", "mixedfx16"):
+            x = torch.zeros_like(b)
+            for _ in range(3):
+                x.zero_()
+                stag.stag_cg(h, x, b, mass, mode=mode)
+            sec, info = _timed(lambda: (x.zero_(), stag.stag_cg(h, x, b, mass, mode=mode))[1], reps=5)
+            res[mode] = {"s": sec, "iters": info["iters"], "true_rel_resid": info["true_rel_resid"]}
+        print(json.dumps({"config": "8^4 single-mass CG, m=0.1, 1e-10", "unit": "s", "results": res}), flush=True)
+        h.free()
+    elif args.config == "multishift":
+        dims, mass = (48, 48, 48, 96), 0.005
+        shifts = [10 ** (-4 + k / 2) for k in range(9)]
+        fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
+        h = stag.stag_load_links(dims, torch.from_numpy(fat).to(dev), torch.from_numpy(lng).to(dev), recon_long=12,
+                                 prec_mask=0b1011)
+        del fat, lng
+        b = torch.from_numpy(synth.gaussian_source(dims, 5000)).to(dev)
+        xs = [torch.zeros_like(b) for _ in shifts]
+        res = {}
+        for mode in ("mixed32", "mixedfx16"):
+            stag.stag_multishift_cg(h, xs, b, mass, shifts, mode=mode)
+            sec, infos = _timed(lambda: stag.stag_multishift_cg(h, xs, b, mass, shifts, mode=mode), reps=2)
+            res[mode] = {"s": sec, "iters": [i["iters"] for i in infos],
+                         "max_true_rel_resid": max(i["true_rel_resid"] for i in infos)}
+        print(json.dumps({"config": "48^3x96 multi-shift CG, 9 shifts 1e-4..1, m=0.005, 1e-10 every shift",
+                          "unit": "s", "results": res}), flush=True)
+        h.free()
+    elif args.config == "batch":
+        dims_list = [(16, 16, 16, 16)] * 4 + [(24, 24, 24, 48)] * 4 + [(32, 32, 32, 32)] * 4
+        masses = [0.01, 0.02, 0.05]
+        items = []
+        for j, dims in enumerate(dims_list):
+            fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED + j)
+            h = stag.stag_load_links(dims, torch.from_numpy(fat).to(dev), torch.from_numpy(lng).to(dev), recon_long=12,
+                                     prec_mask=0b1011)
+            bd = torch.from_numpy(synth.gaussian_source(dims, 5000 + 100 * j, nrhs=8)).to(dev)
+            items.append((h, torch.zeros_like(bd), bd, 8, masses[j % 3]))
+        res = {}
+        for mode in ("mixed32", "mixedfx16"):
+            def batched():
+                for it in items:
+                    it[1].zero_()
+                return stag.stag_batch_solve(items, mode=mode)
+
+            def sequential():
+                out = []
+                for h, x, bd, n, m in items:
+                    x.zero_()
+                    for i in range(n):
+                        out.append(stag.stag_cg(h, x[i], bd[i], m, mode=mode))
+                return out
+
+            batched()
+            tb, ib = _timed(batched, reps=2)
+            sequential()
+            ts, isq = _timed(sequential, reps=1)
+            res[mode] = {"batched_s": tb, "sequential_s": ts, "speedup": ts / tb,
+                         "all_converged": all(i["converged"] for i in ib + isq),
+                         "max_true_rel_resid": max(i["true_rel_resid"] for i in ib)}
+        print(json.dumps({"config": "12 lattices (4x16^4, 4x24^3x48, 4x32^4) x 8 RHS, m in {0.01,0.02,0.05}, 1e-10",
+                          "unit": "s", "results": res}), flush=True)
+        for it in items:
+            it[0].free()
 
 
 def main(argv=None):
@@ -480,9 +583,14 @@ def main(argv=None):
     ap.add_argument("--sweep-precs", nargs="+", default=["fp64", "fp32", "fp16", "fx16"])
     ap.add_argument("--sweep-recons", nargs="+", type=int, default=[18, 12])
     ap.add_argument("--sweep-reps", type=int, default=20)
+    ap.add_argument("--sweep-nrhs", nargs="+", type=int, default=[1])
+    ap.add_argument("--config", default="headline", choices=["headline", "small", "multishift", "batch"])
     args = ap.parse_args(argv)
     if args.dslash_sweep:
         run_dslash_sweep(args)
+        return
+    if args.config != "headline":
+        run_config(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -62,7 +62,16 @@ typedef enum { STAG_FP64 = 0, STAG_FP32 = 1, STAG_FP16 = 2, STAG_FX16 = 3 } stag
  * reductions, FP64 solution accumulation and FP64 "reliable updates" (true
  * residual b - M y recomputed in FP64 whenever the iterated residual has
  * dropped by `delta` since the last update). */
-typedef enum { STAG_PLAIN64 = 0, STAG_MIXED32 = 1, STAG_MIXED16 = 2, STAG_MIXEDFX16 = 3 } stag_mode;
+typedef enum {
+  STAG_PLAIN64 = 0,
+  STAG_MIXED32 = 1,
+  STAG_MIXED16 = 2,
+  STAG_MIXEDFX16 = 3,
+  STAG_LEARNED = 4  /* flexible CG preconditioned by a trained network (params->precond);
+                       sloppy operator in 16-bit fixed point if the handle holds that
+                       copy, else FP32; falls back to mixed CG if FCG breaks down or
+                       reaches max_iter */
+} stag_mode;
 
 typedef struct stag_lattice_s* stag_lattice_t; /* opaque, library-owned */
 
@@ -85,6 +94,7 @@ typedef struct {
   int check_interval;  /* iterations between host convergence checks (>=1) */
   double ms_tol;       /* multi-shift: relative residual at which the shared
                           Krylov loop hands each shift to refinement (<=0: tol) */
+  void* precond;       /* stag_net_t for STAG_LEARNED, else ignored */
 } stag_solve_params;
 
 typedef struct {
@@ -94,6 +104,7 @@ typedef struct {
   int status;           /* STAG_OK or the error for this system */
   double true_rel_resid; /* ||b - M x|| / ||b|| recomputed in FP64 on the GPU */
   double seconds;       /* wall time of the solve on the host */
+  int precond_fallback; /* STAG_LEARNED: 1 if the mixed-CG fallback ran */
 } stag_solve_info;
 
 /* Default parameters: tol 1e-10, max_iter 100000, MIXED32, delta 0.1,
@@ -209,6 +220,57 @@ typedef struct {
  * `stream`. */
 int stag_batch_solve(const stag_batch_item* items, int nitems, const stag_solve_params* params,
                      stag_solve_info* infos, void* stream);
+
+/* ------------------------------------------------------------ learned part
+ * A gauge-covariant network used as a preconditioner z = N(r) inside
+ * flexible CG.  Fields are full-lattice, channels of colour vectors; a layer
+ * with real weights W[d][c][c'] (stored as bfloat16, FP32 accumulation)
+ * computes pre_c = sum_d sum_c' W[d][c][c'] T_d h_c', d = 0 the identity and
+ * d = 1 + 2mu, 2 + 2mu the fat-link hops of the staggered operator from +mu
+ * and -mu (the +-1/2 eta F parts of D); hidden layers apply the covariant
+ * gate v * sigmoid(|v|^2 - b_c).  The residual is scaled to unit mean square
+ * per site and placed on the even sites; the output's even sites, scaled
+ * back, are z.  Parameters, flat FP32 array: for each layer W[9][Cout][Cin]
+ * then (hidden layers) b[Cout].  Widths 1 and 16 are supported, first and
+ * last width 1.  The network needs the handle's FP32 link copy. */
+typedef struct stag_net_s* stag_net_t;
+
+typedef struct {
+  stag_lattice_t lat; /* gauge field of the pair (FP32 copy required) */
+  const void* r;      /* device, canonical [V/2][3] residual */
+  const void* e;      /* device, canonical [V/2][3] error x* - x of that residual */
+} stag_train_pair;
+
+typedef struct {
+  int epochs;
+  int batch;               /* pairs per Adam step (gradients averaged) */
+  double lr;               /* Adam step size (beta1 0.9, beta2 0.999) */
+  unsigned long long seed; /* visiting-order permutations */
+  int pair_prec;           /* STAG_FP64: complex double pairs; STAG_FP32: complex float */
+} stag_train_params;
+
+/* channels: nlayers + 1 widths (e.g. {1, 16, 16, 16, 1}); seed: the small
+ * normal noise of the initial weights.  The network starts near the
+ * identity (self direction maps channel c to c with weight 1, gates open),
+ * so an untrained network makes flexible CG behave like CG. */
+int stag_net_create(stag_net_t* out, const int* channels, int nlayers, unsigned long long seed);
+int stag_net_free(stag_net_t net);
+long long stag_net_num_params(stag_net_t net);
+/* host copies of the parameters; rounded = 1 returns the weights as the
+ * kernels use them (bfloat16 values), 0 the FP32 master copy */
+int stag_net_get_params(stag_net_t net, float* host, long long count, int rounded);
+int stag_net_set_params(stag_net_t net, const float* host, long long count);
+/* z = N(r), r and z device canonical [V/2][3] complex double.  Asynchronous. */
+int stag_net_apply(stag_net_t net, stag_lattice_t lat, void* z, const void* r, void* stream);
+/* loss ||N(r)^ - e^||^2 / ||e^||^2 of one pair (both sides scaled by
+ * sqrt(V/2)/||r||) and its gradient w.r.t. the parameters (host array of
+ * count floats).  Synchronises `stream`. */
+int stag_net_loss_grad(stag_net_t net, stag_lattice_t lat, const void* r, const void* e, double* loss, float* grad,
+                       long long count, void* stream);
+/* Adam training on the pairs (all on lattices of one size); losses: host,
+ * epochs * npairs values in visiting order, may be NULL.  Synchronises. */
+int stag_net_train(stag_net_t net, const stag_train_pair* pairs, int npairs, const stag_train_params* tp,
+                   double* losses, void* stream);
 
 /* Human-readable text of a status code (static storage). */
 const char* stag_strerror(int status);

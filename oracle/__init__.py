@@ -15,6 +15,10 @@ Parity status of each function (what pins it, checked by the CPU tests):
   * multishift_cg          -- dense LU solve per shift on 4^4, and single-mass
                               CG run shift by shift.
   * true_residual          -- exact definition ||b - M x|| / ||b||.
+  * network (module)       -- forward, backward and loss of the gauge-covariant
+                              preconditioner network: finite differences of
+                              the loss, transport adjointness, gauge
+                              covariance (tests/test_network_oracle.py).
   * apply_m_at_sites       -- equals apply_m restricted to the sampled sites
                               (checked on small lattices), used to check
                               full-size GPU results site by site.

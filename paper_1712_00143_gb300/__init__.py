@@ -31,10 +31,16 @@ STAG_ENOTUNITARY = -6
 STAG_ETIMEOUT = -7
 
 STAG_FP64, STAG_FP32, STAG_FP16, STAG_FX16 = 0, 1, 2, 3
-STAG_PLAIN64, STAG_MIXED32, STAG_MIXED16, STAG_MIXEDFX16 = 0, 1, 2, 3
+STAG_PLAIN64, STAG_MIXED32, STAG_MIXED16, STAG_MIXEDFX16, STAG_LEARNED = 0, 1, 2, 3, 4
 
 PREC = {"fp64": STAG_FP64, "fp32": STAG_FP32, "fp16": STAG_FP16, "fx16": STAG_FX16}
-MODE = {"plain64": STAG_PLAIN64, "mixed32": STAG_MIXED32, "mixed16": STAG_MIXED16, "mixedfx16": STAG_MIXEDFX16}
+MODE = {
+    "plain64": STAG_PLAIN64,
+    "mixed32": STAG_MIXED32,
+    "mixed16": STAG_MIXED16,
+    "mixedfx16": STAG_MIXEDFX16,
+    "learned": STAG_LEARNED,
+}
 
 # every entry point declared in include/stag.h
 EXPORTS = (
@@ -49,6 +55,14 @@ EXPORTS = (
     "stag_cg",
     "stag_multishift_cg",
     "stag_batch_solve",
+    "stag_net_create",
+    "stag_net_free",
+    "stag_net_num_params",
+    "stag_net_get_params",
+    "stag_net_set_params",
+    "stag_net_apply",
+    "stag_net_loss_grad",
+    "stag_net_train",
     "stag_strerror",
     "stag_profile_enable",
     "stag_profile_select",
@@ -82,6 +96,7 @@ class SolveParams(ctypes.Structure):
         ("use_initial_guess", ctypes.c_int),
         ("check_interval", ctypes.c_int),
         ("ms_tol", ctypes.c_double),
+        ("precond", ctypes.c_void_p),
     ]
 
 
@@ -95,6 +110,20 @@ class BatchItem(ctypes.Structure):
     ]
 
 
+class TrainPair(ctypes.Structure):
+    _fields_ = [("lat", ctypes.c_void_p), ("r", ctypes.c_void_p), ("e", ctypes.c_void_p)]
+
+
+class TrainParams(ctypes.Structure):
+    _fields_ = [
+        ("epochs", ctypes.c_int),
+        ("batch", ctypes.c_int),
+        ("lr", ctypes.c_double),
+        ("seed", ctypes.c_ulonglong),
+        ("pair_prec", ctypes.c_int),
+    ]
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [
         ("iters", ctypes.c_int),
@@ -103,6 +132,7 @@ class SolveInfo(ctypes.Structure):
         ("status", ctypes.c_int),
         ("true_rel_resid", ctypes.c_double),
         ("seconds", ctypes.c_double),
+        ("precond_fallback", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -132,6 +162,17 @@ def load_library(path=LIB_PATH):
             [vp, ctypes.POINTER(vp), vp, cd, ctypes.POINTER(cd), ci, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), vp],
         ),
         "stag_batch_solve": (ci, [ctypes.POINTER(BatchItem), ci, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), vp]),
+        "stag_net_create": (ci, [ctypes.POINTER(vp), ctypes.POINTER(ci), ci, ctypes.c_ulonglong]),
+        "stag_net_free": (ci, [vp]),
+        "stag_net_num_params": (ctypes.c_longlong, [vp]),
+        "stag_net_get_params": (ci, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_longlong, ci]),
+        "stag_net_set_params": (ci, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_longlong]),
+        "stag_net_apply": (ci, [vp, vp, vp, vp, vp]),
+        "stag_net_loss_grad": (
+            ci,
+            [vp, vp, vp, vp, ctypes.POINTER(cd), ctypes.POINTER(ctypes.c_float), ctypes.c_longlong, vp],
+        ),
+        "stag_net_train": (ci, [vp, ctypes.POINTER(TrainPair), ci, ctypes.POINTER(TrainParams), ctypes.POINTER(cd), vp]),
         "stag_strerror": (ctypes.c_char_p, [ci]),
         "stag_profile_enable": (ci, [ci]),
         "stag_profile_select": (ci, [ctypes.c_char_p, ci]),
@@ -186,6 +227,8 @@ def default_params(**kw):
     for k, v in kw.items():
         if k == "mode" and isinstance(v, str):
             v = MODE[v]
+        if k == "precond" and isinstance(v, NetHandle):
+            v = v.ptr.value
         setattr(p, k, v)
     return p
 
@@ -328,6 +371,106 @@ def stag_batch_solve(items, params=None, stream=None, raise_on_error=True, **kw)
     for d in out:
         d["return"] = st
     return out
+
+
+class NetHandle:
+    """Owns a ``stag_net_t`` (the learned preconditioner's parameters)."""
+
+    def __init__(self, ptr, channels):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.channels = tuple(channels)
+
+    def free(self):
+        if self.ptr and self.ptr.value:
+            _check(_lib.stag_net_free(self.ptr), "stag_net_free")
+            self.ptr = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def stag_net_create(channels=(1, 16, 16, 16, 1), seed=1):
+    ch = (ctypes.c_int * len(channels))(*channels)
+    h = ctypes.c_void_p()
+    _check(_lib.stag_net_create(ctypes.byref(h), ch, len(channels) - 1, int(seed)), "stag_net_create")
+    return NetHandle(h.value, channels)
+
+
+def stag_net_free(net):
+    net.free()
+
+
+def stag_net_num_params(net):
+    return int(_lib.stag_net_num_params(net.ptr))
+
+
+def stag_net_get_params(net, rounded=False):
+    import numpy as np
+
+    n = stag_net_num_params(net)
+    out = np.empty(n, dtype=np.float32)
+    _check(
+        _lib.stag_net_get_params(net.ptr, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n, 1 if rounded else 0),
+        "stag_net_get_params",
+    )
+    return out
+
+
+def stag_net_set_params(net, values):
+    import numpy as np
+
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    _check(_lib.stag_net_set_params(net.ptr, v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), v.size), "stag_net_set_params")
+
+
+def stag_net_apply(net, h, z, r, stream=None):
+    n = h.Vh * 3
+    _check(_lib.stag_net_apply(net.ptr, h.ptr, _ptr(z, "z", n), _ptr(r, "r", n), _stream(stream)), "stag_net_apply")
+    return z
+
+
+def stag_net_loss_grad(net, h, r, e, stream=None):
+    import numpy as np
+
+    n = h.Vh * 3
+    npar = stag_net_num_params(net)
+    g = np.empty(npar, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(
+        _lib.stag_net_loss_grad(net.ptr, h.ptr, _ptr(r, "r", n), _ptr(e, "e", n), ctypes.byref(loss),
+                                g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), npar, _stream(stream)),
+        "stag_net_loss_grad",
+    )
+    return loss.value, g
+
+
+def stag_net_train(net, pairs, epochs=1, batch=4, lr=1e-3, seed=1, stream=None):
+    """pairs: sequence of (handle, r, e) with r, e complex128 or complex64 CUDA tensors [V/2][3].
+    Returns the per-pair losses (epochs * len(pairs), visiting order)."""
+    import numpy as np
+
+    arr = (TrainPair * len(pairs))()
+    prec = None
+    for i, (h, r, e) in enumerate(pairs):
+        for t, nm in ((r, "r"), (e, "e")):
+            if not t.is_cuda or not t.is_contiguous() or t.numel() != h.Vh * 3:
+                raise ValueError(f"pair {i}: {nm} must be a contiguous CUDA tensor of V/2*3 entries")
+        p = STAG_FP64 if r.dtype == torch.complex128 else STAG_FP32 if r.dtype == torch.complex64 else None
+        if p is None or e.dtype != r.dtype or (prec is not None and p != prec):
+            raise ValueError("pairs must all be complex128 or all complex64")
+        prec = p
+        arr[i] = TrainPair(h.ptr.value, r.data_ptr(), e.data_ptr())
+    tp = TrainParams(int(epochs), int(batch), float(lr), int(seed), prec)
+    losses = np.empty(len(pairs) * int(epochs), dtype=np.float64)
+    _check(
+        _lib.stag_net_train(net.ptr, arr, len(pairs), ctypes.byref(tp),
+                            losses.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)),
+        "stag_net_train",
+    )
+    return losses
 
 
 def stag_strerror(status):

@@ -225,6 +225,7 @@ void stag_default_params(stag_solve_params* p) {
   p->use_initial_guess = 0;
   p->check_interval = 16;
   p->ms_tol = 1e-6;
+  p->precond = nullptr;
 }
 
 int stag_profile_enable(int on) {

@@ -389,9 +389,12 @@ static int batch_solve_p(const stag_batch_item* items, int nitems, const stag_so
     const stag_batch_item& I = items[it];
     const size_t n = (size_t)I.lat->g.Vh * 3;
     int r = 0;
+    // 16-bit storage: groups of at most 4 (measured: the 8-vector kernel
+    // is slower per vector than the 4-vector one); FP32/FP64: up to 8
+    const int nmax = (P == 16 || P == 15) ? 4 : 8;
     while (r < I.nrhs) {
       const int left = I.nrhs - r;
-      const int N = left >= 8 ? 8 : left >= 4 ? 4 : 2;
+      const int N = left >= 8 && nmax >= 8 ? 8 : left >= 4 ? 4 : 2;
       std::unique_ptr<GroupBase> g = make_group<P>(N);
       g->lat = I.lat;
       g->shift = I.mass * I.mass;
@@ -562,6 +565,7 @@ static int batch_solve_p(const stag_batch_item* items, int nitems, const stag_so
       inf.converged = g->bb[i] > 0.0 ? (c.rr_true <= c.target) : 1;
       inf.status = g->status ? g->status : (inf.converged ? STAG_OK : STAG_ENOTCONV);
       inf.seconds = t1 - t0;
+      inf.precond_fallback = 0;
       if (!inf.converged && !worst) worst = STAG_ENOTCONV;
     }
   }
@@ -578,7 +582,7 @@ extern "C" int stag_batch_solve(const stag_batch_item* items, int nitems, const 
   stag_solve_params prm;
   stag_default_params(&prm);
   if (params) prm = *params;
-  if (!(prm.tol > 0.0) || prm.max_iter < 0 || prm.mode < 0 || prm.mode > 3) return STAG_EINVAL;
+  if (!(prm.tol > 0.0) || prm.max_iter < 0 || prm.mode < 0 || prm.mode > 3) return STAG_EINVAL;  // no learned mode
   if (prm.mode != STAG_PLAIN64 && !(prm.delta > 0.0 && prm.delta < 1.0)) return STAG_EINVAL;
   const int pi = prm.mode == STAG_PLAIN64 ? STAG_FP64 : prm.mode == STAG_MIXED32 ? STAG_FP32
                : prm.mode == STAG_MIXED16 ? STAG_FP16 : STAG_FX16;

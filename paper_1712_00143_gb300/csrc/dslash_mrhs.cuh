@@ -6,9 +6,10 @@
 // right-hand side the algorithmic bytes fall from 16 links + 2 vectors to
 // 16 links / N + 2 vectors.
 //
-// Multi-RHS vector layout ("MRHS"): the N vectors of a site are contiguous,
-//   P = 64, 32: [Vh][N][3] complex;   P = 16, 15: [Vh][N] 16-byte records,
-// so a neighbour gather reads N consecutive colour vectors.
+// Multi-RHS vector layout ("MRHS"): the N vectors one after the other, each
+// in the single-vector layout of its format (FP32: [3][Vh]; 16 bit: [Vh]
+// records; FP64: [Vh][3]), so that for a fixed right-hand side a warp's loads
+// over 32 consecutive sites stay coalesced.
 #pragma once
 #include "dslash_impl.cuh"
 
@@ -24,54 +25,21 @@ template <int P> __host__ __device__ inline size_t spinorm_bytes(int Vh, int n) 
   return spinor_bytes<P>(Vh) * (size_t)n;
 }
 
-template <int P> struct SpinorLoadM;
 template <int P> struct SpinorLoadM {
   using A2 = typename Prec<P>::A2;
-  using S2 = typename Prec<P>::S2;
-  // P = 64 / 32: [Vh][N][3] complex
+  static __device__ __forceinline__ Spinor<P> one(const SpinorM<P>& f, int r) {
+    return Spinor<P>{(char*)f.v + spinor_bytes<P>(f.Vh) * r, f.Vh};
+  }
   static __device__ __forceinline__ void ld(const SpinorM<P>& f, int s, int r, A2 o[3]) {
-    const S2* p = (const S2*)f.v + ((size_t)s * f.n + r) * 3;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      S2 v = __ldg(p + c);
-      o[c].x = v.x;
-      o[c].y = v.y;
-    }
+    SpinorLoad<P>::ld(one(f, r), s, o);
   }
   static __device__ __forceinline__ void ldw(const SpinorM<P>& f, int s, int r, A2 o[3]) {
-    const S2* p = (const S2*)f.v + ((size_t)s * f.n + r) * 3;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      S2 v = p[c];
-      o[c].x = v.x;
-      o[c].y = v.y;
-    }
+    SpinorLoad<P>::ldw(one(f, r), s, o);
   }
   static __device__ __forceinline__ void st(const SpinorM<P>& f, int s, int r, const A2 o[3]) {
-    S2* p = (S2*)f.v + ((size_t)s * f.n + r) * 3;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      S2 v;
-      v.x = o[c].x;
-      v.y = o[c].y;
-      p[c] = v;
-    }
+    SpinorLoad<P>::st(one(f, r), s, o);
   }
 };
-template <int P> struct SpinorLoadM16 {
-  static __device__ __forceinline__ void ld(const SpinorM<P>& f, int s, int r, float2 o[3]) {
-    SpinorLoad16<P>::unpack(__ldg((const uint4*)f.v + (size_t)s * f.n + r), o);
-  }
-  static __device__ __forceinline__ void ldw(const SpinorM<P>& f, int s, int r, float2 o[3]) {
-    SpinorLoad16<P>::unpack(((const uint4*)f.v)[(size_t)s * f.n + r], o);
-  }
-  static __device__ __forceinline__ void st(const SpinorM<P>& f, int s, int r, const float2 o[3]) {
-    Spinor<P> one{(uint4*)f.v + (size_t)s * f.n + r, 1};
-    SpinorLoad16<P>::st(one, 0, o);
-  }
-};
-template <> struct SpinorLoadM<16> : SpinorLoadM16<16> {};
-template <> struct SpinorLoadM<15> : SpinorLoadM16<15> {};
 
 template <int P> struct DslashArgsM {
   Geom g;

@@ -240,7 +240,7 @@ static int ms_solve(stag_lattice_s* lat, double2* const* x_can, const double2* b
   TRY(cuda_status(cudaMemcpyAsync(hscal, dscal, sizeof(double), cudaMemcpyDeviceToHost, st)));
   TRY(cuda_status(cudaStreamSynchronize(st)));
   const double bb = hscal[0];
-  for (int k = 0; k < ns && infos; ++k) infos[k] = stag_solve_info{0, 0, 0, STAG_OK, 1.0, 0.0};
+  for (int k = 0; k < ns && infos; ++k) infos[k] = stag_solve_info{0, 0, 0, STAG_OK, 1.0, 0.0, 0};
   if (!(bb > 0.0)) {
     for (int k = 0; k < ns; ++k) TRY(launch_zero(x_can[k], sizeof(double2) * 3 * (size_t)Vh, st));
     TRY(cuda_status(cudaStreamSynchronize(st)));
@@ -335,15 +335,21 @@ static int ms_solve(stag_lattice_s* lat, double2* const* x_can, const double2* b
 
 using namespace stag;
 
+namespace stag {
+int learned_solve(stag_lattice_s* lat, double2* x, const double2* b, double mass, const stag_solve_params& prm,
+                  stag_solve_info* info, cudaStream_t st);
+}
+
 static int check_params(const stag_solve_params* p) {
   if (!p) return STAG_EINVAL;
-  if (!(p->tol > 0.0) || p->max_iter < 0 || p->mode < 0 || p->mode > 3) return STAG_EINVAL;
+  if (!(p->tol > 0.0) || p->max_iter < 0 || p->mode < 0 || p->mode > 4) return STAG_EINVAL;
+  if (p->mode == STAG_LEARNED && !p->precond) return STAG_EINVAL;
   if (p->mode != STAG_PLAIN64 && !(p->delta > 0.0 && p->delta < 1.0)) return STAG_EINVAL;
   return STAG_OK;
 }
 
 static int mode_prec(int mode) {
-  return mode == STAG_PLAIN64 ? STAG_FP64 : mode == STAG_MIXED32 ? STAG_FP32 : mode == STAG_MIXED16 ? STAG_FP16 : STAG_FX16;
+  return mode == STAG_PLAIN64 ? STAG_FP64 : mode == STAG_MIXED16 ? STAG_FP16 : mode == STAG_MIXEDFX16 ? STAG_FX16 : STAG_FP32;
 }
 
 extern "C" {
@@ -359,6 +365,8 @@ int stag_cg(stag_lattice_t lat, void* x, const void* b, double mass, const stag_
   if (!lat->links[STAG_FP64].present || !lat->links[mode_prec(prm.mode)].present) return STAG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const double shift = mass * mass;
+  if (info) info->precond_fallback = 0;
+  if (prm.mode == STAG_LEARNED) return learned_solve(lat, (double2*)x, (const double2*)b, mass, prm, info, st);
   switch (prm.mode) {
     case STAG_PLAIN64: return cg_solve<64>(lat, (double2*)x, (const double2*)b, shift, prm, info, st);
     case STAG_MIXED32: return cg_solve<32>(lat, (double2*)x, (const double2*)b, shift, prm, info, st);
@@ -370,6 +378,7 @@ int stag_cg(stag_lattice_t lat, void* x, const void* b, double mass, const stag_
 int stag_multishift_cg(stag_lattice_t lat, void* const* x, const void* b, double mass, const double* shifts,
                        int nshift, const stag_solve_params* params, stag_solve_info* infos, void* stream) {
   if (!lat || !x || !b || !shifts || nshift <= 0 || nshift > MAX_SHIFTS) return STAG_EINVAL;
+  if (params && params->mode == STAG_LEARNED) return STAG_EINVAL;
   for (int k = 0; k < nshift; ++k)
     if (!x[k] || !(shifts[k] >= 0.0)) return STAG_EINVAL;
   stag_solve_params prm;

@@ -1,0 +1,121 @@
+"""Pins of the network oracle (CPU): the backward pass against FP64 finite
+differences of the loss, adjointness of the transports, gauge covariance of
+the network, and the bfloat16 rounding."""
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.network as net
+import synth
+
+DIMS = (4, 4, 4, 6)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    fat, lng, thin = synth.gauge_field(DIMS, 0.3, 1010, return_thin=True)
+    even = oracle.parity_sites(DIMS, 0)
+    r = synth.random_spinor(DIMS, 21)
+    e = synth.random_spinor(DIMS, 22)
+    return fat, thin, even, r, e
+
+
+def test_transport_adjoints(setup):
+    fat, thin, even, r, e = setup
+    V = fat.shape[0]
+    a = synth.random_spinor(DIMS, 31, full=True).reshape(1, V, 3)
+    b = synth.random_spinor(DIMS, 32, full=True).reshape(1, V, 3)
+    for d in range(net.NDIR):
+        lhs = np.vdot(a, net.transport(fat, b, DIMS, d))
+        rhs = np.vdot(net.transport_adjoint(fat, a, DIMS, d), b)
+        assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_transports_sum_to_the_fat_part_of_dslash(setup):
+    """sum_{d != 0} T_d h restricted to odd sites = D_oe h with the Naik links set to zero."""
+    fat, thin, even, r, e = setup
+    V = fat.shape[0]
+    h = np.zeros((1, V, 3), dtype=np.complex128)
+    h[0, even] = r
+    tot = sum(net.transport(fat, h, DIMS, d) for d in range(1, net.NDIR))
+    odd = oracle.parity_sites(DIMS, 1)
+    want = oracle.dslash(fat, np.zeros_like(fat), r, DIMS, out_parity=1)
+    assert np.abs(tot[0, odd] - want).max() < 1e-14
+    assert np.abs(tot[0, even]).max() == 0.0
+
+
+@pytest.mark.parametrize("channels", [(1, 2, 1), (1, 3, 2, 1)])
+def test_backward_matches_finite_differences(setup, channels):
+    fat, thin, even, r, e = setup
+    params = net.init_params(channels, 5)
+    params = [(W, None if b is None else b + 0.3) for W, b in params]
+    L, grads = net.backward(fat, params, r, e, DIMS, even)
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    for li, (W, b) in enumerate(params):
+        for _ in range(4):
+            idx = tuple(rng.integers(0, n) for n in W.shape)
+            Wp = W.copy()
+            Wp[idx] += h
+            Wm = W.copy()
+            Wm[idx] -= h
+            pp = list(params)
+            pp[li] = (Wp, b)
+            Lp = net.loss(fat, pp, r, e, DIMS, even)[0]
+            pp[li] = (Wm, b)
+            Lm = net.loss(fat, pp, r, e, DIMS, even)[0]
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - grads[li][0][idx]) < 1e-6 * max(1.0, abs(fd)), (li, idx, fd, grads[li][0][idx])
+        if b is not None:
+            for c in range(len(b)):
+                bp, bm = b.copy(), b.copy()
+                bp[c] += h
+                bm[c] -= h
+                pp = list(params)
+                pp[li] = (W, bp)
+                Lp = net.loss(fat, pp, r, e, DIMS, even)[0]
+                pp[li] = (W, bm)
+                Lm = net.loss(fat, pp, r, e, DIMS, even)[0]
+                fd = (Lp - Lm) / (2 * h)
+                assert abs(fd - grads[li][1][c]) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_network_is_gauge_covariant(setup):
+    fat, thin, even, r, e = setup
+    params = net.init_params((1, 4, 4, 1), 7)
+    params = [(W, None if b is None else b - 0.2) for W, b in params]
+    g = synth.random_gauge_transform(DIMS, 44)
+    fat2, _ = synth.links_from_thin(DIMS, synth.gauge_transform_links(DIMS, thin, g))
+    gr = np.einsum("nij,nj->ni", g[even], r)
+    z1, _ = net.forward(fat, params, r, DIMS, even)
+    z2, _ = net.forward(fat2, params, gr, DIMS, even)
+    assert np.abs(z2 - np.einsum("nij,nj->ni", g[even], z1)).max() < 1e-12 * np.abs(z1).max()
+
+
+def test_planted_wrong_adjoint_fails_finite_differences(setup, monkeypatch):
+    fat, thin, even, r, e = setup
+    params = net.init_params((1, 2, 1), 5)
+    monkeypatch.setattr(net, "transport_adjoint", lambda f, g, dims, d: net.transport(f, g, dims, d))
+    L, grads = net.backward(fat, params, r, e, DIMS, even)
+    W, b = params[0]
+    bad = 0
+    for idx in [(1, 0, 0), (3, 1, 0), (6, 0, 0)]:
+        Wp, Wm = W.copy(), W.copy()
+        Wp[idx] += 1e-6
+        Wm[idx] -= 1e-6
+        Lp = net.loss(fat, [(Wp, b)] + params[1:], r, e, DIMS, even)[0]
+        Lm = net.loss(fat, [(Wm, b)] + params[1:], r, e, DIMS, even)[0]
+        bad += abs((Lp - Lm) / 2e-6 - grads[0][0][idx]) > 1e-4
+    assert bad > 0
+
+
+def test_bf16_rounding():
+    # bfloat16 keeps 8 significant bits: near 1 the spacing is 2^-7
+    vals = np.array([1.0, 1 + 2.0**-8, 1 + 3 * 2.0**-8, 1 + 1.5 * 2.0**-8, -3.14159265, 1e-3])
+    got = net.bf16_round(vals)
+    assert got[0] == 1.0
+    assert got[1] == 1.0  # exact tie: to even
+    assert got[2] == 1 + 2 * 2.0**-7  # exact tie: to even (upwards here)
+    assert got[3] == 1 + 2.0**-7
+    assert np.all(np.abs(got - vals) <= np.abs(vals) * 2.0**-8)
