@@ -493,7 +493,9 @@ def run_config(args):
     """Secondary workloads of the paper's CG path, one JSON line each (not the
     headline): `small` 8^4 FP64 CG; `multishift` 48^3x96 nine-shift CG;
     `batch` 12 lattices x 8 right-hand sides in one batched call vs one
-    stag_cg per system."""
+    stag_cg per system; `learned` training and evaluating the network
+    preconditioner on 32^4; `netpass` one network forward and one
+    loss-and-gradient pass on 32^4."""
     import torch
 
     import paper_1712_00143_gb300 as stag
@@ -569,6 +571,103 @@ def run_config(args):
                           "unit": "s", "results": res}), flush=True)
         for it in items:
             it[0].free()
+    elif args.config == "netpass":
+        # one network forward (z = N(r)) and one loss-and-gradient pass on 32^4
+        dims = (32, 32, 32, 32)
+        fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
+        h = stag.stag_load_links(dims, torch.from_numpy(fat).to(dev), torch.from_numpy(lng).to(dev), recon_long=12,
+                                 prec_mask=0b0010)
+        del fat, lng
+        net = stag.stag_net_create((1, 16, 16, 16, 1), seed=1)
+        r = torch.from_numpy(synth.random_spinor(dims, 1)).to(dev)
+        e = torch.from_numpy(synth.random_spinor(dims, 2)).to(dev)
+        z = torch.empty_like(r)
+        stag.stag_net_apply(net, h, z, r)
+        stag.stag_net_loss_grad(net, h, r, e)
+        t_f, _ = _timed(lambda: stag.stag_net_apply(net, h, z, r), reps=5)
+        t_b, _ = _timed(lambda: stag.stag_net_loss_grad(net, h, r, e), reps=3)
+        stag.stag_profile_reset()
+        stag.stag_profile_enable(True)
+        stag.stag_net_loss_grad(net, h, r, e)
+        fam = {f: stag.stag_profile_read(f) for f in ("net", "net_bwd")}
+        stag.stag_profile_enable(False)
+        flops_fw = 0
+        ch = (1, 16, 16, 16, 1)
+        for l in range(4):
+            # per site: 8 transports (66 flop) per input channel + 9 x Cin x Cout real-by-complex-3 mixes (12 flop)
+            flops_fw += 2 * h.Vh * (8 * ch[l] * 66 + 9 * ch[l] * ch[l + 1] * 12)
+        print(json.dumps({"config": "network 1-16-16-16-1 on 32^4", "forward_s": t_f, "loss_grad_s": t_b,
+                          "forward_gflops": flops_fw / t_f / 1e9,
+                          "families_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in fam.items()}}), flush=True)
+        net.free()
+        h.free()
+    elif args.config == "learned":
+        # 32^4, m = 0.01: 2000 (residual, error) pairs from the unpreconditioned
+        # mixed CG on 24 training fields, network 1-16-16-16-1 trained on the
+        # GPU, flexible CG with it on 8 held-out fields vs mixed CG
+        import numpy as np
+
+        from paper_1712_00143_gb300.learned import make_pairs
+
+        dims, mass = (32, 32, 32, 32), 0.01
+        ntrain, nheld, npairs = args.learned_fields, 8, args.learned_pairs
+        per = -(-npairs // ntrain)
+        t0 = time.perf_counter()
+        handles, pairs = [], []
+        for j in range(ntrain):
+            fat, lng = synth.gauge_field(dims, EPS, 1000 + j)
+            h = stag.stag_load_links(dims, torch.from_numpy(fat).to(dev), torch.from_numpy(lng).to(dev), recon_long=12,
+                                     prec_mask=0b0011)
+            del fat, lng
+            handles.append(h)
+            b = torch.from_numpy(synth.gaussian_source(dims, 5000 + 100 * j)).to(dev)
+            ks = np.unique(np.linspace(1, 470, per).astype(int))
+            pairs += make_pairs(h, [b], mass, ks)
+        pairs = pairs[:npairs]
+        t_pairs = time.perf_counter() - t0
+        net = stag.stag_net_create((1, 16, 16, 16, 1), seed=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = stag.stag_net_train(net, pairs, epochs=args.learned_epochs, batch=8, lr=1e-3, seed=1)
+        t_train = time.perf_counter() - t0
+        del pairs
+        for h in handles:
+            h.free()
+        torch.cuda.empty_cache()
+        raw = stag.stag_net_create((1, 16, 16, 16, 1), seed=1)
+        held = []
+        for j in range(nheld):
+            fat, lng = synth.gauge_field(dims, EPS, 2000 + j)
+            h = stag.stag_load_links(dims, torch.from_numpy(fat).to(dev), torch.from_numpy(lng).to(dev), recon_long=12)
+            del fat, lng
+            b = torch.from_numpy(synth.gaussian_source(dims, 5000 + 100 * (2000 + j))).to(dev)
+            row = {}
+            for name, kw in (("mixedfx16", {"mode": "mixedfx16"}), ("plain64", {"mode": "plain64"}),
+                             ("learned_fcg", {"mode": "learned", "precond": net}),
+                             ("untrained_fcg", {"mode": "learned", "precond": raw})):
+                x = torch.zeros_like(b)
+                stag.stag_cg(h, x, b, mass, tol=TOL, **kw)  # warm
+                x.zero_()
+                sec, info = _timed(lambda: stag.stag_cg(h, x, b, mass, tol=TOL, **kw))
+                row[name] = {"s": sec, "iters": info["iters"], "true_rel_resid": info["true_rel_resid"],
+                             "fallback": info["precond_fallback"]}
+            held.append(row)
+            h.free()
+        summ = {k: {"mean_s": float(np.mean([r[k]["s"] for r in held])),
+                    "mean_iters": float(np.mean([r[k]["iters"] for r in held])),
+                    "all_converged": all(r[k]["true_rel_resid"] <= TOL for r in held),
+                    "fallbacks": int(sum(r[k]["fallback"] for r in held))} for k in held[0]}
+        nl = len(losses) // args.learned_epochs
+        print(json.dumps({"config": f"32^4 m=0.01 learned preconditioner: {len(losses)//args.learned_epochs} pairs from "
+                                    f"{ntrain} training fields, {args.learned_epochs} epochs, {nheld} held-out fields",
+                          "pair_generation_s": t_pairs, "training_s": t_train,
+                          "loss_first_epoch": float(np.mean(losses[:nl])), "loss_last_epoch": float(np.mean(losses[-nl:])),
+                          "held_out": summ,
+                          "iteration_gain_vs_untrained": summ["untrained_fcg"]["mean_iters"] / summ["learned_fcg"]["mean_iters"],
+                          "iteration_gain_vs_mixed_cg": summ["mixedfx16"]["mean_iters"] / summ["learned_fcg"]["mean_iters"]}),
+              flush=True)
+        net.free()
+        raw.free()
 
 
 def main(argv=None):
@@ -584,7 +683,11 @@ def main(argv=None):
     ap.add_argument("--sweep-recons", nargs="+", type=int, default=[18, 12])
     ap.add_argument("--sweep-reps", type=int, default=20)
     ap.add_argument("--sweep-nrhs", nargs="+", type=int, default=[1])
-    ap.add_argument("--config", default="headline", choices=["headline", "small", "multishift", "batch"])
+    ap.add_argument("--config", default="headline",
+                    choices=["headline", "small", "multishift", "batch", "learned", "netpass"])
+    ap.add_argument("--learned-pairs", type=int, default=2000)
+    ap.add_argument("--learned-fields", type=int, default=24)
+    ap.add_argument("--learned-epochs", type=int, default=2)
     args = ap.parse_args(argv)
     if args.dslash_sweep:
         run_dslash_sweep(args)
