@@ -25,14 +25,26 @@ mean-square per site, r_hat = r * sqrt(Vh) / ||r||, placed on the even sites
 of a one-channel field (zeros on odd sites); the prediction is the even-site
 part of the output channel, and z = N(r) = prediction * ||r|| / sqrt(Vh).
 
+Two training losses, both on the scaled fields:
+    error space     L_e = ||z_hat - e_hat||^2 / ||e_hat||^2
+    residual space  L_r = ||M z_hat - r_hat||^2 / ||r_hat||^2
+with M = m^2 - D_eo D_oe the even-odd operator of the pair's gauge field and
+mass.  Since r = M e, L_r = ||M (z_hat - e_hat)||^2 / ||M e_hat||^2: the
+error weighted by M^2, which stresses the high modes a network of a few
+nearest-neighbour hops can represent; L_e is dominated by the low modes that
+make up most of e at small mass.
+
 Gradients use the convention G = dL/dRe + i dL/dIm for complex fields, so a
 linear map y = A h has G_h = A^dag G_y.
 
-Parity status: forward, backward and loss are pinned by finite differences
-of the loss in FP64 and by gauge covariance (tests/test_network_oracle.py).
+Parity status: forward, backward and both losses are pinned by finite
+differences of the loss in FP64 and by gauge covariance
+(tests/test_network_oracle.py).
 """
 
 import numpy as np
+
+from . import staggered
 
 NDIR = 9
 
@@ -126,15 +138,12 @@ def loss(fat, params, r, e, dims, parity_sites):
     return float(np.linalg.norm(diff) ** 2 / ne2), cache
 
 
-def backward(fat, params, r, e, dims, parity_sites):
-    """(loss, grads) with grads a list of (dW, db) matching params."""
-    L, cache = loss(fat, params, r, e, dims, parity_sites)
-    scale = cache["scale"]
+def backward_from(fat, params, cache, g_pred, dims, parity_sites):
+    """Gradients of a loss whose derivative with respect to the scaled even-site
+    prediction z_hat is g_pred ([Vh][3]); returns a list of (dW, db)."""
     V = fat.shape[0]
-    ehat = e * scale
-    pred = cache["h"][-1][0, parity_sites]
     g = np.zeros((1, V, 3), dtype=np.complex128)
-    g[0, parity_sites] = 2.0 * (pred - ehat) / (np.linalg.norm(ehat) ** 2)
+    g[0, parity_sites] = g_pred
     grads = [None] * len(params)
     for li in range(len(params) - 1, -1, -1):
         W, b = params[li]
@@ -155,7 +164,34 @@ def backward(fat, params, r, e, dims, parity_sites):
             gin += transport_adjoint(fat, np.einsum("ab,avi->bvi", W[d], g), dims, d)
         grads[li] = (dW, db)
         g = gin
-    return L, grads
+    return grads
+
+
+def backward(fat, params, r, e, dims, parity_sites):
+    """(L_e, grads) with grads a list of (dW, db) matching params."""
+    L, cache = loss(fat, params, r, e, dims, parity_sites)
+    ehat = e * cache["scale"]
+    pred = cache["h"][-1][0, parity_sites]
+    g_pred = 2.0 * (pred - ehat) / (np.linalg.norm(ehat) ** 2)
+    return L, backward_from(fat, params, cache, g_pred, dims, parity_sites)
+
+
+def loss_residual(fat, lng, params, r, mass, dims, parity_sites):
+    """L_r = ||M z_hat - r_hat||^2 / ||r_hat||^2 with M = m^2 - D_eo D_oe."""
+    z, cache = forward(fat, params, r, dims, parity_sites)
+    zhat = cache["h"][-1][0, parity_sites]
+    rhat = r * cache["scale"]
+    diff = staggered.apply_m(fat, lng, zhat, mass, dims) - rhat
+    cache["resid_diff"] = diff
+    return float(np.linalg.norm(diff) ** 2 / np.linalg.norm(rhat) ** 2), cache
+
+
+def backward_residual(fat, lng, params, r, mass, dims, parity_sites):
+    """(L_r, grads): dL_r/dz_hat = 2 M (M z_hat - r_hat) / ||r_hat||^2 (M is Hermitian)."""
+    L, cache = loss_residual(fat, lng, params, r, mass, dims, parity_sites)
+    rhat = r * cache["scale"]
+    g_pred = 2.0 * staggered.apply_m(fat, lng, cache["resid_diff"], mass, dims) / np.linalg.norm(rhat) ** 2
+    return L, backward_from(fat, params, cache, g_pred, dims, parity_sites)
 
 
 def init_params(channels, seed):

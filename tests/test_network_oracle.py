@@ -119,3 +119,82 @@ def test_bf16_rounding():
     assert got[2] == 1 + 2 * 2.0**-7  # exact tie: to even (upwards here)
     assert got[3] == 1 + 2.0**-7
     assert np.all(np.abs(got - vals) <= np.abs(vals) * 2.0**-8)
+
+
+MASS = 0.07
+
+
+@pytest.fixture(scope="module")
+def with_long():
+    fat, lng = synth.gauge_field(DIMS, 0.3, 1010)
+    return fat, lng
+
+
+@pytest.mark.parametrize("channels", [(1, 2, 1), (1, 3, 2, 1)])
+def test_residual_loss_backward_matches_finite_differences(setup, with_long, channels):
+    fat, thin, even, r, e = setup
+    fat, lng = with_long
+    params = net.init_params(channels, 6)
+    params = [(W, None if b is None else b + 0.2) for W, b in params]
+    L, grads = net.backward_residual(fat, lng, params, r, MASS, DIMS, even)
+    rng = np.random.default_rng(3)
+    h = 1e-6
+    for li, (W, b) in enumerate(params):
+        idxs = [tuple(rng.integers(0, n) for n in W.shape) for _ in range(4)]
+        for idx in idxs:
+            Wp, Wm = W.copy(), W.copy()
+            Wp[idx] += h
+            Wm[idx] -= h
+            pp = list(params)
+            pp[li] = (Wp, b)
+            Lp = net.loss_residual(fat, lng, pp, r, MASS, DIMS, even)[0]
+            pp[li] = (Wm, b)
+            Lm = net.loss_residual(fat, lng, pp, r, MASS, DIMS, even)[0]
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - grads[li][0][idx]) < 1e-6 * max(1.0, abs(fd)), (li, idx, fd, grads[li][0][idx])
+        if b is not None:
+            bp, bm = b.copy(), b.copy()
+            bp[0] += h
+            bm[0] -= h
+            pp = list(params)
+            pp[li] = (W, bp)
+            Lp = net.loss_residual(fat, lng, pp, r, MASS, DIMS, even)[0]
+            pp[li] = (W, bm)
+            Lm = net.loss_residual(fat, lng, pp, r, MASS, DIMS, even)[0]
+            assert abs((Lp - Lm) / (2 * h) - grads[li][1][0]) < 1e-6 * max(1.0, abs(grads[li][1][0]))
+
+
+def test_residual_loss_of_a_scaled_identity_is_a_least_squares_fit(setup, with_long):
+    """A single linear layer with only the self direction, weight w, gives
+    z = w r, so L_r(w) = ||w M r^ - r^||^2 / ||r^||^2: a quadratic in w whose
+    minimum sits at w* = Re<M r^, r^> / ||M r^||^2 with value
+    1 - Re<M r^, r^>^2 / (||M r^||^2 ||r^||^2), where dL/dw vanishes."""
+    fat, thin, even, r, e = setup
+    fat, lng = with_long
+    rhat = r * np.sqrt(len(even)) / np.linalg.norm(r)
+    Mr = oracle.apply_m(fat, lng, rhat, MASS, DIMS)
+    a = np.vdot(Mr, rhat).real
+    w_star = a / np.linalg.norm(Mr) ** 2
+    W = np.zeros((net.NDIR, 1, 1))
+    W[0, 0, 0] = w_star
+    L, grads = net.backward_residual(fat, lng, [(W, None)], r, MASS, DIMS, even)
+    want = 1.0 - a * a / (np.linalg.norm(Mr) ** 2 * np.linalg.norm(rhat) ** 2)
+    assert abs(L - want) < 1e-12
+    assert abs(grads[0][0][0, 0, 0]) < 1e-10
+    # away from w*: the quadratic, exactly
+    W[0, 0, 0] = 2.0 * w_star
+    L2 = net.loss_residual(fat, lng, [(W, None)], r, MASS, DIMS, even)[0]
+    assert abs(L2 - np.linalg.norm(2.0 * w_star * Mr - rhat) ** 2 / np.linalg.norm(rhat) ** 2) < 1e-12
+
+
+def test_residual_loss_equals_m_weighted_error(setup, with_long):
+    """With r = M e the residual loss is ||M (z^ - e^)||^2 / ||M e^||^2."""
+    fat, thin, even, r, e = setup
+    fat, lng = with_long
+    r = oracle.apply_m(fat, lng, e, MASS, DIMS)
+    params = net.init_params((1, 2, 1), 8)
+    L, cache = net.loss_residual(fat, lng, params, r, MASS, DIMS, even)
+    s = cache["scale"]
+    zhat = cache["h"][-1][0, even]
+    want = np.linalg.norm(oracle.apply_m(fat, lng, zhat - e * s, MASS, DIMS)) ** 2 / np.linalg.norm(r * s) ** 2
+    assert abs(L - want) < 1e-11 * max(1.0, want)
