@@ -247,7 +247,19 @@ typedef struct {
   double lr;               /* Adam step size (beta1 0.9, beta2 0.999) */
   unsigned long long seed; /* visiting-order permutations */
   int pair_prec;           /* STAG_FP64: complex double pairs; STAG_FP32: complex float */
+  int loss;                /* stag_loss */
+  double mass;             /* the pairs' mass m (STAG_LOSS_RESIDUAL) */
 } stag_train_params;
+
+/* Training losses, both on the scaled fields r^ = r sqrt(V/2)/||r||, e^, z^ = N^(r^):
+ *   STAG_LOSS_RESIDUAL  ||M z^ - r^||^2 / ||r^||^2, M = m^2 - D_eo D_oe of the
+ *                       pair's field in FP32 (= ||M (z^ - e^)||^2 / ||M e^||^2
+ *                       since r = M e: the error weighted by M^2, i.e. by the
+ *                       high modes a short-range network can represent)
+ *   STAG_LOSS_ERROR     ||z^ - e^||^2 / ||e^||^2 (dominated by the low modes
+ *                       that make up most of e at small mass; at m = 0.01 it
+ *                       barely falls below 1) */
+enum stag_loss { STAG_LOSS_ERROR = 0, STAG_LOSS_RESIDUAL = 1 };
 
 /* channels: nlayers + 1 widths (e.g. {1, 16, 16, 16, 1}); seed: the small
  * normal noise of the initial weights.  The network starts near the
@@ -262,11 +274,12 @@ int stag_net_get_params(stag_net_t net, float* host, long long count, int rounde
 int stag_net_set_params(stag_net_t net, const float* host, long long count);
 /* z = N(r), r and z device canonical [V/2][3] complex double.  Asynchronous. */
 int stag_net_apply(stag_net_t net, stag_lattice_t lat, void* z, const void* r, void* stream);
-/* loss ||N(r)^ - e^||^2 / ||e^||^2 of one pair (both sides scaled by
- * sqrt(V/2)/||r||) and its gradient w.r.t. the parameters (host array of
- * count floats).  Synchronises `stream`. */
-int stag_net_loss_grad(stag_net_t net, stag_lattice_t lat, const void* r, const void* e, double* loss, float* grad,
-                       long long count, void* stream);
+/* Loss of one pair (loss_kind: stag_loss; mass: the pair's m, used by
+ * STAG_LOSS_RESIDUAL) and its gradient w.r.t. the parameters (host array of
+ * count floats).  r, e: device canonical [V/2][3] complex double.
+ * Synchronises `stream`. */
+int stag_net_loss_grad(stag_net_t net, stag_lattice_t lat, const void* r, const void* e, int loss_kind, double mass,
+                       double* loss, float* grad, long long count, void* stream);
 /* Adam training on the pairs (all on lattices of one size); losses: host,
  * epochs * npairs values in visiting order, may be NULL.  Synchronises. */
 int stag_net_train(stag_net_t net, const stag_train_pair* pairs, int npairs, const stag_train_params* tp,

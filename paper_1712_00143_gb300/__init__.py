@@ -121,7 +121,12 @@ class TrainParams(ctypes.Structure):
         ("lr", ctypes.c_double),
         ("seed", ctypes.c_ulonglong),
         ("pair_prec", ctypes.c_int),
+        ("loss", ctypes.c_int),
+        ("mass", ctypes.c_double),
     ]
+
+
+LOSS = {"error": 0, "residual": 1}
 
 
 class SolveInfo(ctypes.Structure):
@@ -170,7 +175,7 @@ def load_library(path=LIB_PATH):
         "stag_net_apply": (ci, [vp, vp, vp, vp, vp]),
         "stag_net_loss_grad": (
             ci,
-            [vp, vp, vp, vp, ctypes.POINTER(cd), ctypes.POINTER(ctypes.c_float), ctypes.c_longlong, vp],
+            [vp, vp, vp, vp, ci, cd, ctypes.POINTER(cd), ctypes.POINTER(ctypes.c_float), ctypes.c_longlong, vp],
         ),
         "stag_net_train": (ci, [vp, ctypes.POINTER(TrainPair), ci, ctypes.POINTER(TrainParams), ctypes.POINTER(cd), vp]),
         "stag_strerror": (ctypes.c_char_p, [ci]),
@@ -432,23 +437,27 @@ def stag_net_apply(net, h, z, r, stream=None):
     return z
 
 
-def stag_net_loss_grad(net, h, r, e, stream=None):
+def stag_net_loss_grad(net, h, r, e, loss="residual", mass=0.0, stream=None):
+    """Loss of one (r, e) pair and its gradient (host float32 array).  loss:
+    "residual" (||M z^ - r^||^2 / ||r^||^2, needs the pair's mass) or "error"."""
     import numpy as np
 
     n = h.Vh * 3
     npar = stag_net_num_params(net)
     g = np.empty(npar, dtype=np.float32)
-    loss = ctypes.c_double()
+    out = ctypes.c_double()
     _check(
-        _lib.stag_net_loss_grad(net.ptr, h.ptr, _ptr(r, "r", n), _ptr(e, "e", n), ctypes.byref(loss),
+        _lib.stag_net_loss_grad(net.ptr, h.ptr, _ptr(r, "r", n), _ptr(e, "e", n), LOSS[loss], float(mass),
+                                ctypes.byref(out),
                                 g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), npar, _stream(stream)),
         "stag_net_loss_grad",
     )
-    return loss.value, g
+    return out.value, g
 
 
-def stag_net_train(net, pairs, epochs=1, batch=4, lr=1e-3, seed=1, stream=None):
+def stag_net_train(net, pairs, epochs=1, batch=4, lr=1e-3, seed=1, loss="residual", mass=0.0, stream=None):
     """pairs: sequence of (handle, r, e) with r, e complex128 or complex64 CUDA tensors [V/2][3].
+    loss: "residual" (needs the pairs' mass) or "error".
     Returns the per-pair losses (epochs * len(pairs), visiting order)."""
     import numpy as np
 
@@ -463,7 +472,7 @@ def stag_net_train(net, pairs, epochs=1, batch=4, lr=1e-3, seed=1, stream=None):
             raise ValueError("pairs must all be complex128 or all complex64")
         prec = p
         arr[i] = TrainPair(h.ptr.value, r.data_ptr(), e.data_ptr())
-    tp = TrainParams(int(epochs), int(batch), float(lr), int(seed), prec)
+    tp = TrainParams(int(epochs), int(batch), float(lr), int(seed), prec, LOSS[loss], float(mass))
     losses = np.empty(len(pairs) * int(epochs), dtype=np.float64)
     _check(
         _lib.stag_net_train(net.ptr, arr, len(pairs), ctypes.byref(tp),

@@ -122,6 +122,56 @@ __global__ void k_net_loss(const float2* __restrict__ hL, Spinor<32> e, const do
   grid_reduce<1>(v, rb, tgt);
 }
 
+// Residual-space loss, step 1: the scaled prediction z^ (even block of the
+// output channel) as an FP32 structure-of-arrays field.
+__global__ void k_net_pred_to_spinor(const float2* __restrict__ hL, Spinor<32> z) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < z.Vh; s += gridDim.x * blockDim.x) {
+    float2 o[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[c] = hL[(size_t)s * 3 + c];
+    SpinorLoad<32>::st(z, s, o);
+  }
+}
+
+// Step 2: diff = M z^ - r^ (mz = M z^, r^ = r * scale), loss numerator
+// ||diff||^2 / ||r^||^2 (||r^||^2 = scale^2 ||r||^2) reduced into `tgt`.
+__global__ void k_net_resid_loss(Spinor<32> mz, Spinor<32> r, const double* __restrict__ rr, Spinor<32> diff, RedBuf rb,
+                                 RedTarget tgt) {
+  const int Vh = r.Vh;
+  const double sc2 = (double)Vh / fmax(*rr, 1e-300);
+  const float sc = (float)sqrt(sc2);
+  Acc1<float> acc;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+    float2 a[3], b[3], o[3];
+    SpinorLoad<32>::ld(mz, s, a);
+    SpinorLoad<32>::ld(r, s, b);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      o[c] = make_float2(a[c].x - b[c].x * sc, a[c].y - b[c].y * sc);
+      acc.add_prod(o[c].x, o[c].x);
+      acc.add_prod(o[c].y, o[c].y);
+    }
+    SpinorLoad<32>::st(diff, s, o);
+  }
+  double v[1] = {acc.value() / (sc2 * fmax(*rr, 1e-300))};
+  grid_reduce<1>(v, rb, tgt);
+}
+
+// Step 3: the output-channel gradient 2 M diff / ||r^||^2 on even sites, 0 on odd.
+__global__ void k_net_resid_grad(Spinor<32> mdiff, float2* __restrict__ g) {
+  const int Vh = mdiff.Vh;
+  const float k = 2.f / (float)Vh;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+    float2 a[3];
+    SpinorLoad<32>::ld(mdiff, s, a);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      g[(size_t)s * 3 + c] = make_float2(k * a[c].x, k * a[c].y);
+      g[((size_t)Vh + s) * 3 + c] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
 int grid_for(int n, int block) {
   int g = (n + block - 1) / block;
   return g < 8192 ? g : 8192;
@@ -279,19 +329,53 @@ int net_apply(stag_net_s* net, stag_lattice_s* lat, Spinor<32> z, Spinor<32> r, 
   return last_launch_status();
 }
 
-// Loss of one (r, e) pair and its gradient added to net->grad.
-static int net_loss_grad(NetRun& R, Spinor<32> r, Spinor<32> e, double* loss_dev, cudaStream_t st) {
+// M v = m^2 v - D_eo D_oe v in FP32 (t: odd-parity scratch).
+static int apply_m32(stag_lattice_s* lat, Spinor<32> out, Spinor<32> v, Spinor<32> t, double m2, RedScratch rs,
+                     cudaStream_t st) {
+  TRYN(launch_dslash<32>(lat, t, v, 1, nullptr, st));
+  return launch_dslash_epi<32>(lat, out, t, 0, v, m2, Spinor<32>{nullptr, v.Vh}, 0.0, -1.0, 0, rs,
+                               RedTarget{RED_STORE, nullptr, nullptr}, nullptr, st);
+}
+
+// Loss of one (r, e) pair (kind: stag_loss) and its gradient added to net->grad.
+static int net_loss_grad(NetRun& R, Spinor<32> r, Spinor<32> e, int kind, double mass, double* loss_dev,
+                         cudaStream_t st) {
   stag_net_s* N = R.net;
   TRYN(launch_norm2<32>(r, R.rs, RedTarget{RED_STORE, nullptr, R.scal}, st));
-  TRYN(launch_norm2<32>(e, R.rs, RedTarget{RED_STORE, nullptr, R.scal + 1}, st));
+  if (kind == STAG_LOSS_ERROR) TRYN(launch_norm2<32>(e, R.rs, RedTarget{RED_STORE, nullptr, R.scal + 1}, st));
   TRYN(net_forward(R, r, R.scal, st));
-  {
+  const int G = grid_for(R.Vh, 256) < R.rs.max_grid ? grid_for(R.Vh, 256) : R.rs.max_grid;
+  if (kind == STAG_LOSS_ERROR) {
     ProfScope ps("net_bwd", st);
-    k_net_loss<<<grid_for(R.Vh, 256) < R.rs.max_grid ? grid_for(R.Vh, 256) : R.rs.max_grid, 256, 0, st>>>(
-        R.h[N->nl], e, R.scal, R.scal + 1, R.g0, RedBuf{R.rs.partials, R.rs.counter},
-        RedTarget{RED_STORE, nullptr, loss_dev});
+    k_net_loss<<<G, 256, 0, st>>>(R.h[N->nl], e, R.scal, R.scal + 1, R.g0, RedBuf{R.rs.partials, R.rs.counter},
+                                  RedTarget{RED_STORE, nullptr, loss_dev});
+    TRYN(last_launch_status());
+  } else {
+    int s = 0;
+    Spinor<32> z = ws_spinor<32>(R.lat, "netloss.z", &s);
+    Spinor<32> mz = ws_spinor<32>(R.lat, "netloss.mz", &s);
+    Spinor<32> t = ws_spinor<32>(R.lat, "netloss.t", &s);
+    if (s) return s;
+    const double m2 = mass * mass;
+    {
+      ProfScope ps("net_bwd", st);
+      k_net_pred_to_spinor<<<grid_for(R.Vh, 256), 256, 0, st>>>(R.h[N->nl], z);
+    }
+    TRYN(last_launch_status());
+    TRYN(apply_m32(R.lat, mz, z, t, m2, R.rs, st));
+    {
+      ProfScope ps("net_bwd", st);
+      k_net_resid_loss<<<G, 256, 0, st>>>(mz, r, R.scal, z, RedBuf{R.rs.partials, R.rs.counter},
+                                          RedTarget{RED_STORE, nullptr, loss_dev});
+    }
+    TRYN(last_launch_status());
+    TRYN(apply_m32(R.lat, mz, z, t, m2, R.rs, st));  // M (M z^ - r^)
+    {
+      ProfScope ps("net_bwd", st);
+      k_net_resid_grad<<<grid_for(R.Vh, 256), 256, 0, st>>>(mz, R.g0);
+    }
+    TRYN(last_launch_status());
   }
-  TRYN(last_launch_status());
   float2 *g = R.g0, *gin = R.g1;
   for (int l = N->nl - 1; l >= 0; --l) {
     TRYN(layer_bwd(R, l, g, gin, l > 0, st));
@@ -427,9 +511,11 @@ int stag_net_apply(stag_net_t n, stag_lattice_t lat, void* z, const void* r, voi
   return launch_to_canonical<32>((double2*)z, zs, lat->g.Vh, st);
 }
 
-int stag_net_loss_grad(stag_net_t n, stag_lattice_t lat, const void* r, const void* e, double* loss, float* grad,
-                       long long count, void* stream) {
+int stag_net_loss_grad(stag_net_t n, stag_lattice_t lat, const void* r, const void* e, int loss_kind, double mass,
+                       double* loss, float* grad, long long count, void* stream) {
   if (!n || !lat || !r || !e || !loss || !grad || count != (long long)n->nparam) return STAG_EINVAL;
+  if (loss_kind != STAG_LOSS_ERROR && loss_kind != STAG_LOSS_RESIDUAL) return STAG_EINVAL;
+  if (loss_kind == STAG_LOSS_RESIDUAL && !(mass >= 0.0)) return STAG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   NetRun R;
   TRYN(net_run_init(n, lat, R, true));
@@ -440,7 +526,7 @@ int stag_net_loss_grad(stag_net_t n, stag_lattice_t lat, const void* r, const vo
   TRYN(launch_from_canonical<32>(rs, (const double2*)r, lat->g.Vh, st));
   TRYN(launch_from_canonical<32>(es, (const double2*)e, lat->g.Vh, st));
   TRYN(cuda_status(cudaMemsetAsync(n->grad, 0, n->nparam * 4, st)));
-  TRYN(net_loss_grad(R, rs, es, R.scal + 2, st));
+  TRYN(net_loss_grad(R, rs, es, loss_kind, mass, R.scal + 2, st));
   TRYN(cuda_status(cudaMemcpyAsync(loss, R.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, st)));
   TRYN(cuda_status(cudaMemcpyAsync(grad, n->grad, n->nparam * 4, cudaMemcpyDeviceToHost, st)));
   return cuda_status(cudaStreamSynchronize(st));
@@ -450,6 +536,8 @@ int stag_net_train(stag_net_t n, const stag_train_pair* pairs, int npairs, const
                    double* losses, void* stream) {
   if (!n || !pairs || npairs <= 0 || !tp || tp->epochs <= 0 || tp->batch <= 0) return STAG_EINVAL;
   if (tp->pair_prec != STAG_FP64 && tp->pair_prec != STAG_FP32) return STAG_EINVAL;
+  if (tp->loss != STAG_LOSS_ERROR && tp->loss != STAG_LOSS_RESIDUAL) return STAG_EINVAL;
+  if (tp->loss == STAG_LOSS_RESIDUAL && !(tp->mass >= 0.0)) return STAG_EINVAL;
   for (int i = 0; i < npairs; ++i)
     if (!pairs[i].lat || !pairs[i].r || !pairs[i].e || pairs[i].lat->g.Vh != pairs[0].lat->g.Vh) return STAG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -481,7 +569,7 @@ int stag_net_train(stag_net_t n, const stag_train_pair* pairs, int npairs, const
         TRYN(canon_to_sloppy(P.lat, es, P.e, STAG_FP32, st));
       }
       if (inbatch == 0) TRYN(cuda_status(cudaMemsetAsync(n->grad, 0, n->nparam * 4, st)));
-      TRYN(net_loss_grad(R, rs, es, lossd + (size_t)ep * npairs + k, st));
+      TRYN(net_loss_grad(R, rs, es, tp->loss, tp->mass, lossd + (size_t)ep * npairs + k, st));
       if (++inbatch == tp->batch || k == npairs - 1) {
         n->step += 1;
         const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);

@@ -80,14 +80,20 @@ def test_forward_matches_oracle(small):
     assert rel_l2(z.cpu().numpy(), zo) < 2e-5
 
 
-def test_gradient_matches_oracle(small):
+@pytest.mark.parametrize("kind", ["error", "residual"])
+def test_gradient_matches_oracle(small, kind):
     stag = _stag()
     dims, fat, lng, thin, h, net = small
+    mass = 0.05
     r = synth.random_spinor(dims, 52)
     e = synth.random_spinor(dims, 53)
-    loss, g = stag.stag_net_loss_grad(net, h, dev(r), dev(e))
+    loss, g = stag.stag_net_loss_grad(net, h, dev(r), dev(e), loss=kind, mass=mass)
     params = _oracle_params(stag.stag_net_get_params(net, rounded=True), CH)
-    lo, go = onet.backward(fat, params, r, e, dims, oracle.parity_sites(dims, 0))
+    even = oracle.parity_sites(dims, 0)
+    if kind == "error":
+        lo, go = onet.backward(fat, params, r, e, dims, even)
+    else:
+        lo, go = onet.backward_residual(fat, lng, params, r, mass, dims, even)
     go = _flat_grads(go)
     assert abs(loss - lo) < 1e-5 * abs(lo)
     assert np.linalg.norm(g - go) / np.linalg.norm(go) < 1e-4
@@ -146,7 +152,7 @@ def trained():
         srcs = [dev(synth.gaussian_source(dims, 7000 + 10 * j + s)) for s in range(2)]
         pairs += make_pairs(h, srcs, mass, iters=[1, 3, 6, 10, 15, 22, 30, 40])
     net = stag.stag_net_create(CH, seed=5)
-    losses = stag.stag_net_train(net, pairs, epochs=6, batch=4, lr=2e-3, seed=2)
+    losses = stag.stag_net_train(net, pairs, epochs=6, batch=4, lr=2e-3, seed=2, loss="residual", mass=mass)
     yield dims, mass, net, losses, len(pairs)
     net.free()
     for h in handles:
@@ -154,15 +160,15 @@ def trained():
 
 
 def test_training_lowers_the_loss(trained):
-    """The relative error loss falls over the epochs.  It stays near 1: the
-    error of a CG iterate is dominated by low modes that a network reaching
-    four hops cannot resolve; what the network does learn shows in the
-    iteration count of flexible CG (next test)."""
+    """The residual-space loss ||M N(r) - r||^2 / ||r||^2 starts far above 1
+    (the near-identity network returns about r, and M is not near the
+    identity) and must fall well below its start and below 1."""
     dims, mass, net, losses, npairs = trained
     first = losses[:npairs].mean()
     last = losses[-npairs:].mean()
     assert np.all(np.isfinite(losses))
-    assert last < first, (first, last)
+    print(f"residual loss: first epoch {first:.4f}, last epoch {last:.4f}")
+    assert last < 0.5 * first and last < 1.0, (first, last)
 
 
 def test_learned_fcg_converges_and_gains(trained):
