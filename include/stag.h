@@ -285,6 +285,15 @@ int stag_net_loss_grad(stag_net_t net, stag_lattice_t lat, const void* r, const 
 int stag_net_train(stag_net_t net, const stag_train_pair* pairs, int npairs, const stag_train_params* tp,
                    double* losses, void* stream);
 
+/* Check of this build's tensor-core path on the current GPU (the path the
+ * network's 16 -> 16 layers take): one tile of tcgen05 bfloat16 products
+ * with FP32 accumulation in tensor memory, 9 accumulated steps, compared
+ * with the same sums on the CUDA cores.  *max_rel_err: max |difference| /
+ * max |reference| (0 expected: the test values are exact in both).
+ * STAG_ETIMEOUT if a bounded wait gave up.  Synchronous.  No counterpart in
+ * the paper, which predates these tensor cores. */
+int stag_tc_selftest(double* max_rel_err);
+
 /* Human-readable text of a status code (static storage). */
 const char* stag_strerror(int status);
 

@@ -63,6 +63,7 @@ EXPORTS = (
     "stag_net_apply",
     "stag_net_loss_grad",
     "stag_net_train",
+    "stag_tc_selftest",
     "stag_strerror",
     "stag_profile_enable",
     "stag_profile_select",
@@ -178,6 +179,7 @@ def load_library(path=LIB_PATH):
             [vp, vp, vp, vp, ci, cd, ctypes.POINTER(cd), ctypes.POINTER(ctypes.c_float), ctypes.c_longlong, vp],
         ),
         "stag_net_train": (ci, [vp, ctypes.POINTER(TrainPair), ci, ctypes.POINTER(TrainParams), ctypes.POINTER(cd), vp]),
+        "stag_tc_selftest": (ci, [ctypes.POINTER(cd)]),
         "stag_strerror": (ctypes.c_char_p, [ci]),
         "stag_profile_enable": (ci, [ci]),
         "stag_profile_select": (ci, [ctypes.c_char_p, ci]),
@@ -480,6 +482,13 @@ def stag_net_train(net, pairs, epochs=1, batch=4, lr=1e-3, seed=1, loss="residua
         "stag_net_train",
     )
     return losses
+
+
+def stag_tc_selftest():
+    """Max relative error of one tensor-core tile against the CUDA cores (0 expected)."""
+    err = ctypes.c_double()
+    _check(_lib.stag_tc_selftest(ctypes.byref(err)), "stag_tc_selftest")
+    return err.value
 
 
 def stag_strerror(status):

@@ -7,7 +7,7 @@
 #include <cstring>
 #include <vector>
 
-#include "net_kernels.cuh"
+#include "net_tc.cuh"
 
 struct stag_net_s {
   int nl = 0;
@@ -233,7 +233,30 @@ static void launch_layer(const NetRun& R, int l, const float2* in, float2* pre, 
                          const float* b, int transpose, cudaStream_t st) {
   const int n = 2 * R.Vh;
   count_launch();
-  k_net_layer<CIN, COUT, GATE><<<(n + 127) / 128, 128, 0, st>>>(R.ng, in, pre, out, W, b, transpose);
+  if constexpr (CIN == 16 && COUT == 16) {
+    // the channel mixing of a 16 -> 16 layer runs on the tensor cores
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_net_layer_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+      cudaFuncSetAttribute(k_net_layer_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+      attr = true;
+    }
+    const int tiles = 2 * ((R.Vh + tc::TILE - 1) / tc::TILE);
+    k_net_layer_tc<GATE><<<tiles, 128, tc::SMEM_BYTES, st>>>(R.ng, in, pre, out, W, b, transpose);
+  } else {
+    k_net_layer<CIN, COUT, GATE><<<(n + 127) / 128, 128, 0, st>>>(R.ng, in, pre, out, W, b, transpose);
+  }
+}
+
+// STAG_ETIMEOUT if a tensor-core layer gave up a bounded wait since the
+// last check (the flag is cleared here).  Synchronous.
+static int net_tc_status() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, tc::g_tc_error, sizeof(int)) != cudaSuccess) return STAG_ECUDA;
+  if (!v) return STAG_OK;
+  v = 0;
+  cudaMemcpyToSymbol(tc::g_tc_error, &v, sizeof(int));
+  return STAG_ETIMEOUT;
 }
 
 // Layer l forward (ch[l] -> ch[l+1]); supported widths 1 and 16.
@@ -529,7 +552,27 @@ int stag_net_loss_grad(stag_net_t n, stag_lattice_t lat, const void* r, const vo
   TRYN(net_loss_grad(R, rs, es, loss_kind, mass, R.scal + 2, st));
   TRYN(cuda_status(cudaMemcpyAsync(loss, R.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, st)));
   TRYN(cuda_status(cudaMemcpyAsync(grad, n->grad, n->nparam * 4, cudaMemcpyDeviceToHost, st)));
-  return cuda_status(cudaStreamSynchronize(st));
+  TRYN(cuda_status(cudaStreamSynchronize(st)));
+  return net_tc_status();
+}
+
+int stag_tc_selftest(double* max_rel_err) {
+  if (!max_rel_err) return STAG_EINVAL;
+  float* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return STAG_ENOMEM;
+  }
+  cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+  count_launch();
+  k_tc_selftest<<<1, 128, tc::SMEM_BYTES>>>(d);
+  int s = last_launch_status();
+  float h[2] = {0.f, 0.f};
+  if (!s) s = cuda_status(cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost));
+  cudaFree(d);
+  if (s) return s;
+  *max_rel_err = h[0];
+  return h[1] == 1.f ? STAG_OK : STAG_ETIMEOUT;
 }
 
 int stag_net_train(stag_net_t n, const stag_train_pair* pairs, int npairs, const stag_train_params* tp,
@@ -586,7 +629,8 @@ int stag_net_train(stag_net_t n, const stag_train_pair* pairs, int npairs, const
   }
   if (losses)
     TRYN(cuda_status(cudaMemcpyAsync(losses, lossd, sizeof(double) * (size_t)npairs * tp->epochs, cudaMemcpyDeviceToHost, st)));
-  return cuda_status(cudaStreamSynchronize(st));
+  TRYN(cuda_status(cudaStreamSynchronize(st)));
+  return net_tc_status();
 }
 
 }  // extern "C"
@@ -623,7 +667,7 @@ struct FcgState {
   double pr_re, pr_im;     // <p, r>
   double alpha_re, alpha_im;
   double pap_prev;
-  int first;               // 1: no previous direction (start, reliable update)
+  int first;               // 1: no previous direction yet
 };
 
 namespace fcgk {
@@ -688,11 +732,15 @@ __global__ void k_fcg_dir(Spinor<P> p, Spinor<32> z, Spinor<32> r, FcgState* fs,
   grid_reduce<2>(v, rb, RedTarget{RED_STORE, nullptr, &fs->pr_re});
 }
 
-// alpha = <p, r> / <p, Ap> (pAp reduced by the operator epilogue into cg.pAp)
+// alpha = <p, r> / <p, Ap> (pAp reduced by the operator epilogue into cg.pAp).
+// <p, r> = <z, r> in exact arithmetic (r is orthogonal to the previous
+// direction), so Re<p, r> <= 0 means N(r) is no descent direction: the
+// network is not acting as a positive preconditioner and the solve is
+// handed to the fallback at once.
 __global__ void k_fcg_alpha(FcgState* fs) {
   if (stopped(&fs->cg.flags)) return;
   const double pap = fs->cg.pAp;
-  if (!(pap > 0.0) || !isfinite(pap)) {
+  if (!(pap > 0.0) || !isfinite(pap) || !(fs->pr_re > 0.0)) {
     fs->cg.flags |= F_BREAKDOWN;
     return;
   }
@@ -730,7 +778,6 @@ __global__ void k_fcg_update(Spinor<32> x, Spinor<32> r, Spinor<P> p, Spinor<32>
 }
 
 __global__ void k_fcg_clear_first(FcgState* fs) { fs->first = 0; }
-__global__ void k_fcg_set_first(FcgState* fs) { fs->first = 1; }
 
 int red_grid_n(int Vh, int cap) {
   int g = (Vh + 255) / 256;
@@ -847,6 +894,7 @@ static int fcg_solve(stag_lattice_s* lat, stag_net_s* net, double2* x_can, const
       TRYN(cuda_status(cudaMemcpyAsync(hs, dst, sizeof(FcgState), cudaMemcpyDeviceToHost, st)));
       TRYN(cuda_status(cudaStreamSynchronize(st)));
       prof_flush_completed();
+      TRYN(net_tc_status());
       if (hs->cg.flags & F_BREAKDOWN) {
         status = STAG_EBREAKDOWN;
         break;
@@ -861,10 +909,9 @@ static int fcg_solve(stag_lattice_s* lat, stag_net_s* net, double2* x_can, const
       if (hs->cg.flags & (F_CONVERGED | F_NEED_RU | F_ITER_CAP)) {
         TRYN(launch_accumulate<32>(y64, xh, st));
         TRYN(true_residual(RedTarget{RED_RU_RESID, &dst->cg, nullptr}));
+        // the direction is kept (as in CG's reliable update): the next one is
+        // made A-orthogonal to it whatever the residual
         TRYN(launch_convert<32, 64>(rh, r64, st));
-        count_launch();
-        k_fcg_set_first<<<1, 1, 0, st>>>(dst);
-        TRYN(last_launch_status());
         TRYN(cuda_status(cudaMemcpyAsync(hs, dst, sizeof(FcgState), cudaMemcpyDeviceToHost, st)));
         TRYN(cuda_status(cudaStreamSynchronize(st)));
         if (hs->cg.flags & F_BREAKDOWN) {

@@ -36,17 +36,21 @@ __device__ __forceinline__ const float2* act_ptr(const float2* a, int C, int Vh,
 __device__ __forceinline__ void load_hop_matrix(const NetGeom& ng, int p, int s, int d, float2 w[9]) {
   const int mu = (d - 1) >> 1;
   const int k0 = mu * ng.cpm + ((d & 1) ? 0 : 9);  // FP32: 2 complex per chunk
-  const uint4* L = ng.links[p];
+  const uint4* L = p ? ng.links[1] : ng.links[0];
   const int Vh = ng.g.Vh;
+  // chunks c0 .. c0 + 4 hold entries 2 c0 .. 2 c0 + 9; the matrix starts at
+  // the first entry (k0 even) or the second (k0 odd).  Indices into w stay
+  // compile-time constants so that w lives in registers.
+  const bool odd = k0 & 1;
+  const uint4* src = L + (size_t)(k0 >> 1) * Vh + s;
 #pragma unroll
   for (int j = 0; j < 5; ++j) {
-    const int k = k0 + 2 * j - (k0 & 1);  // chunk holding entries k, k+1
-    uint4 c = __ldg(L + (size_t)(k >> 1) * Vh + s);
-    float2 a = make_float2(__uint_as_float(c.x), __uint_as_float(c.y));
-    float2 b = make_float2(__uint_as_float(c.z), __uint_as_float(c.w));
-    const int e0 = k - k0, e1 = k + 1 - k0;
-    if (e0 >= 0 && e0 < 9) w[e0] = a;
-    if (e1 >= 0 && e1 < 9) w[e1] = b;
+    const uint4 c = __ldg(src + (size_t)j * Vh);
+    const float2 a = make_float2(__uint_as_float(c.x), __uint_as_float(c.y));
+    const float2 b = make_float2(__uint_as_float(c.z), __uint_as_float(c.w));
+    if (j > 0) w[2 * j - 1] = odd ? a : w[2 * j - 1];
+    if (j < 4) w[2 * j + 1] = odd ? w[2 * j + 1] : b;
+    w[2 * j] = odd ? b : a;
   }
 }
 
@@ -99,6 +103,33 @@ __global__ void __launch_bounds__(128) k_net_layer(NetGeom ng, const float2* __r
     float2 w[9];
     if (d) load_hop_matrix(ng, p, s, d, w);
     const float2* src = act_ptr(hin, CIN, Vh, np, ns);
+    if constexpr (COUT == 1 && CIN > 1) {
+      // one output channel: mix first, then transport once (T_d is linear
+      // and the weights are real, so sum_c' W T_d h_c' = T_d sum_c' W h_c')
+      float2 m[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      const float* wr = sw + d * CIN;
+#pragma unroll 4
+      for (int cp = 0; cp < CIN; ++cp) {
+        const float k = wr[cp];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float2 v = __ldg(src + cp * 3 + i);
+          m[i].x = fmaf(k, v.x, m[i].x);
+          m[i].y = fmaf(k, v.y, m[i].y);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (d) {
+#pragma unroll
+          for (int j = 0; j < 3; ++j) cmac(acc[0][i], w[3 * i + j], m[j]);
+        } else {
+          acc[0][i].x += m[i].x;
+          acc[0][i].y += m[i].y;
+        }
+      }
+      continue;
+    }
 #pragma unroll 4
     for (int cp = 0; cp < CIN; ++cp) {
       float2 v[3], t[3];

@@ -1,0 +1,446 @@
+// net_tc.cuh -- the 16 -> 16 channel layers of the preconditioner network on
+// the fifth-generation tensor cores (tcgen05, accumulators in tensor memory).
+//
+// A layer computes pre_c(x) = sum_d sum_c' W[d][c][c'] (T_d h_c')(x).  For a
+// tile of 64 sites of one parity this is, per direction d, the product
+//     D[row][c] += sum_c' X_d[row][c'] W_d[c][c']
+// with row = (colour-and-re/im component j, site) -- 6 x 64 = 384 rows, real
+// weights act on real and imaginary parts alike -- K = 16 input channels and
+// N = 16 output channels: three 128 x 16 x 16 MMAs per direction, nine
+// directions accumulated in one tensor-memory accumulator of 3 x 16 columns.
+// The CUDA cores compute the transports X_d (3x3 complex link times colour
+// vector, FP32) and write them to shared memory as bfloat16 in two parts,
+// hi = bf16(x) and lo = bf16(x - hi), so hi + lo carries 16 significant bits
+// and the product with the bfloat16 weights is accurate to about 2^-17 (each
+// part is multiplied exactly and accumulated in FP32).  Directions are
+// double-buffered: the transports of d + 1 are written while the MMAs of d
+// run; an mbarrier signalled by tcgen05.commit guards buffer reuse.
+//
+// Shared-memory operand layout (no swizzle, K-major): 8-row x 16-byte core
+// matrices stored as 128 contiguous bytes; the two 16-byte K halves of a row
+// group are 128 bytes apart (leading byte offset) and consecutive row groups
+// 256 bytes apart (stride byte offset).
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "net_kernels.cuh"
+
+namespace stag {
+namespace tc {
+
+constexpr int TILE = 64;                    // sites per CTA tile
+constexpr int ROWS = 6 * TILE;              // 384 MMA rows
+constexpr int A_BYTES = ROWS * 16 * 2;      // one operand part of one direction: 12288 B
+constexpr int B_BYTES = 16 * 16 * 2;        // weights of one direction: 512 B
+constexpr int TMEM_COLS = 64;               // 3 x 16 accumulator columns, allocated as 64
+constexpr int E_STRIDE = 97;                // floats per site in the epilogue staging (96 + 1 pad)
+constexpr int SMEM_BYTES = 4 * A_BYTES + NET_NDIR * B_BYTES + 64;
+
+static_assert(TILE * E_STRIDE * 4 <= 4 * A_BYTES, "epilogue staging must fit in the operand buffers");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// UMMA shared-memory descriptor: start address, leading / stride byte
+// offsets (all >> 4), descriptor version 1 (bits 46-47), no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B bfloat16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the completion of the phase with the given parity:
+// gives up after about `cycles` SM clocks and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long cycles) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > cycles) return false;
+  return true;
+}
+
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Whole warp: allocate `ncols` tensor-memory columns; the address lands in *dst.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+// Whole warp: release the columns.
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// One thread: D[tmem] (+)= A[adesc] x B[bdesc]^T.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// One thread: arrive on *bar once every tcgen05 operation it issued so far has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// Whole warp: 16 consecutive FP32 columns of the warp's 32 lanes (lane field of taddr = 32 * (warp % 4)).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (row, k) in a K-major no-swizzle operand with
+// 16-element (32-byte) rows: core matrix (row / 8, k / 8).
+__host__ __device__ __forceinline__ int op_offset(int row, int k) {
+  return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// hi = bf16(x), lo = bf16(x - hi), two values packed per 32-bit word.
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
+  const __nv_bfloat16 al = __float2bfloat16_rn(a - __bfloat162float(ah));
+  const __nv_bfloat16 bl = __float2bfloat16_rn(b - __bfloat162float(bh));
+  hi = (uint32_t)__bfloat16_as_ushort(ah) | ((uint32_t)__bfloat16_as_ushort(bh) << 16);
+  lo = (uint32_t)__bfloat16_as_ushort(al) | ((uint32_t)__bfloat16_as_ushort(bl) << 16);
+}
+
+__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+
+__device__ int g_tc_error;  // set (never cleared by kernels) when a bounded wait gave up
+
+constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds at GB300 clocks
+
+}  // namespace tc
+
+// 16 -> 16 layer on the tensor cores.  transpose != 0: the adjoint layer
+// (weights W'[d][c][c'] = sign(d) W[partner(d)][c'][c]).  GATE: hout =
+// pre * sigmoid(|pre|^2 - b_c) and pre stored; else hout = pre.
+template <bool GATE>
+__global__ void __launch_bounds__(128, 4)
+    k_net_layer_tc(NetGeom ng, const float2* __restrict__ hin, float2* __restrict__ pre, float2* __restrict__ hout,
+                   const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias, int transpose) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* A = tc_smem;                                // [buffer 2][part 2][A_BYTES]
+  unsigned char* Bw = tc_smem + 4 * A_BYTES;                 // [9][B_BYTES]
+  uint64_t* bar = (uint64_t*)(Bw + NET_NDIR * B_BYTES);   // [2]
+  uint32_t* tmem_slot = (uint32_t*)(bar + 2);
+  int* s_ok = (int*)(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int Vh = ng.g.Vh;
+  const int tiles_per_parity = (Vh + TILE - 1) / TILE;
+  const int p = blockIdx.x / tiles_per_parity;
+  const int s0 = (blockIdx.x - p * tiles_per_parity) * TILE;
+
+  // weights -> B operand (N = output channel c, K = input channel c')
+  for (int i = tid; i < NET_NDIR * 256; i += blockDim.x) {
+    const int d = i >> 8, c = (i >> 4) & 15, cp = i & 15;
+    float w;
+    if (!transpose) {
+      w = __bfloat162float(W[i]);
+    } else {
+      const int dd = d == 0 ? 0 : ((d & 1) ? d + 1 : d - 1);
+      w = (d == 0 ? 1.f : -1.f) * __bfloat162float(W[(dd * 16 + cp) * 16 + c]);
+    }
+    *(__nv_bfloat16*)(Bw + d * B_BYTES + op_offset(c, cp)) = __float2bfloat16_rn(w);
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    *s_ok = 1;
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t IDESC = idesc_bf16(128, 16);
+
+  // staging role: site s_local, channel half `half` (8 input channels)
+  const int s_local = tid & 63, half = tid >> 6;
+  const int s = s0 + s_local;
+  const bool valid = s < Vh;
+  const uint32_t a_base = smem_u32(A);
+
+#pragma unroll 1
+  for (int d = 0; d < NET_NDIR; ++d) {
+    const int buf = d & 1;
+    if (d >= 2) {
+      // the MMAs of direction d - 2 read this buffer: wait for them
+      if (tid == 0 && *s_ok && !mbar_wait(&bar[buf], (uint32_t)(((d - 2) >> 1) & 1), WAIT_CYCLES)) *s_ok = 0;
+      __syncthreads();
+    }
+    const uint32_t hi_base = a_base + (uint32_t)(buf * 2 + 0) * A_BYTES;
+    const uint32_t lo_base = a_base + (uint32_t)(buf * 2 + 1) * A_BYTES;
+    float2 w[9];
+    const float2* src = nullptr;
+    if (valid) {
+      int np, ns;
+      net_neighbour(ng, p, s, d, np, ns);
+      if (d) load_hop_matrix(ng, p, s, d, w);
+      src = act_ptr(hin, 16, Vh, np, ns) + half * 24;
+    }
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      float2 t[4][3];
+      if (valid) {
+        const float4* s4 = (const float4*)(src + g * 12);
+        float2 v[4][3];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const float4 u = __ldg(s4 + q);
+          v[(2 * q) / 3][(2 * q) % 3] = make_float2(u.x, u.y);
+          v[(2 * q + 1) / 3][(2 * q + 1) % 3] = make_float2(u.z, u.w);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (d) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              t[c][i] = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int j = 0; j < 3; ++j) cmac(t[c][i], w[3 * i + j], v[c][j]);
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) t[c][i] = v[c][i];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) t[c][i] = make_float2(0.f, 0.f);
+      }
+      // rows j * 64 + s_local, j = 2 * colour + (0: re, 1: im); K = half * 8 + g * 4 + 0..3
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int i = j >> 1;
+        float x[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = (j & 1) ? t[c][i].y : t[c][i].x;
+        uint32_t h0, l0, h1, l1;
+        split2(x[0], x[1], h0, l0);
+        split2(x[2], x[3], h1, l1);
+        const uint32_t off = (uint32_t)op_offset(j * TILE + s_local, half * 8 + g * 4);
+        st_shared_v2(hi_base + off, h0, h1);
+        st_shared_v2(lo_base + off, l0, l1);
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0 && *s_ok) {
+      tc_fence_after();
+      const uint64_t bdesc = smem_desc(smem_u32(Bw + d * B_BYTES), 128, 256);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const uint32_t dcol = tmem + 16 * b;
+        mma_bf16(dcol, smem_desc(hi_base + b * 4096, 128, 256), bdesc, IDESC, d > 0 ? 1u : 0u);
+        mma_bf16(dcol, smem_desc(lo_base + b * 4096, 128, 256), bdesc, IDESC, 1u);
+      }
+      mma_commit(&bar[buf]);
+    }
+  }
+  // the last commit (direction 8, buffer 0, its fifth phase) covers every MMA
+  if (tid == 0 && *s_ok && !mbar_wait(&bar[0], 0u, WAIT_CYCLES)) *s_ok = 0;
+  __syncthreads();
+  tc_fence_after();
+  const bool ok = *s_ok != 0;
+  float* E = (float*)tc_smem;  // reuses the operand buffers: [64 sites][E_STRIDE]
+  if (ok) {
+    // warp w holds rows 32 w .. 32 w + 31 of each 128-row block b:
+    // colour b, component w / 2 (re, im), sites 32 (w % 2) + lane
+    const int sl = 32 * (warp & 1) + lane, comp = warp >> 1;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * b, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) E[sl * E_STRIDE + c * 6 + b * 2 + comp] = v[c];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(&tc::g_tc_error, 1);
+    return;
+  }
+  for (int q = tid; q < TILE * 16; q += blockDim.x) {
+    const int sl = q >> 4, c = q & 15;
+    const int site = s0 + sl;
+    if (site >= Vh) continue;
+    const float* e = E + sl * E_STRIDE + c * 6;
+    float2 v[3] = {make_float2(e[0], e[1]), make_float2(e[2], e[3]), make_float2(e[4], e[5])};
+    float2* ho = act_ptr(hout, 16, Vh, p, site) + c * 3;
+    if (GATE) {
+      const float n2 = v[0].x * v[0].x + v[0].y * v[0].y + v[1].x * v[1].x + v[1].y * v[1].y + v[2].x * v[2].x +
+                       v[2].y * v[2].y;
+      const float sg = 1.f / (1.f + __expf(-(n2 - bias[c])));
+      float2* po = act_ptr(pre, 16, Vh, p, site) + c * 3;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        po[i] = v[i];
+        ho[i] = make_float2(v[i].x * sg, v[i].y * sg);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) ho[i] = v[i];
+    }
+  }
+}
+
+// Check of the tensor-core path on this GPU: one tile (384 x 16 rows of
+// bfloat16 hi/lo operands from a fixed integer pattern, 9 accumulated
+// K = 16 steps) against the same products summed by the CUDA cores in FP32.
+// out[0] = max |D_tc - D_ref| / max |D_ref|, out[1] = 1 if every wait ended.
+__global__ void __launch_bounds__(128, 1) k_tc_selftest(float* out) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* A = tc_smem;
+  unsigned char* Bw = tc_smem + 4 * A_BYTES;
+  uint64_t* bar = (uint64_t*)(Bw + NET_NDIR * B_BYTES);
+  uint32_t* tmem_slot = (uint32_t*)(bar + 2);
+  int* s_ok = (int*)(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto aval = [](int d, int row, int k, int part) {  // exactly representable values
+    const int h = (d * 7 + row * 13 + k * 5) % 17 - 8;
+    return part == 0 ? (float)h * 0.125f : (float)((row + k + d) % 5 - 2) * (1.f / 4096.f);
+  };
+  auto bval = [](int d, int n, int k) { return (float)((d * 3 + n * 11 + k * 7) % 13 - 6) * 0.0625f; };
+  for (int i = tid; i < NET_NDIR * 256; i += blockDim.x) {
+    const int d = i >> 8, n = (i >> 4) & 15, k = i & 15;
+    *(__nv_bfloat16*)(Bw + d * B_BYTES + op_offset(n, k)) = __float2bfloat16_rn(bval(d, n, k));
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    *s_ok = 1;
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t IDESC = idesc_bf16(128, 16);
+  const uint32_t a_base = smem_u32(A);
+#pragma unroll 1
+  for (int d = 0; d < NET_NDIR; ++d) {
+    const int buf = d & 1;
+    if (d >= 2) {
+      if (tid == 0 && *s_ok && !mbar_wait(&bar[buf], (uint32_t)(((d - 2) >> 1) & 1), WAIT_CYCLES)) *s_ok = 0;
+      __syncthreads();
+    }
+    for (int i = tid; i < ROWS * 16; i += blockDim.x) {
+      const int row = i >> 4, k = i & 15;
+      for (int part = 0; part < 2; ++part)
+        *(__nv_bfloat16*)(A + (buf * 2 + part) * A_BYTES + op_offset(row, k)) =
+            __float2bfloat16_rn(aval(d, row, k, part));
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0 && *s_ok) {
+      tc_fence_after();
+      const uint64_t bdesc = smem_desc(smem_u32(Bw + d * B_BYTES), 128, 256);
+      for (int b = 0; b < 3; ++b) {
+        mma_bf16(tmem + 16 * b, smem_desc(a_base + (buf * 2) * A_BYTES + b * 4096, 128, 256), bdesc, IDESC,
+                 d > 0 ? 1u : 0u);
+        mma_bf16(tmem + 16 * b, smem_desc(a_base + (buf * 2 + 1) * A_BYTES + b * 4096, 128, 256), bdesc, IDESC, 1u);
+      }
+      mma_commit(&bar[buf]);
+    }
+  }
+  if (tid == 0 && *s_ok && !mbar_wait(&bar[0], 0u, WAIT_CYCLES)) *s_ok = 0;
+  __syncthreads();
+  tc_fence_after();
+  float err = 0.f, ref_max = 0.f;
+  if (*s_ok) {
+    for (int b = 0; b < 3; ++b) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * b, v);
+      const int row = 128 * b + 32 * warp + lane;
+      for (int n = 0; n < 16; ++n) {
+        float ref = 0.f;
+        for (int d = 0; d < NET_NDIR; ++d)
+          for (int k = 0; k < 16; ++k) ref += (aval(d, row, k, 0) + aval(d, row, k, 1)) * bval(d, n, k);
+        err = fmaxf(err, fabsf(v[n] - ref));
+        ref_max = fmaxf(ref_max, fabsf(ref));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    err = fmaxf(err, __shfl_xor_sync(0xffffffffu, err, o));
+    ref_max = fmaxf(ref_max, __shfl_xor_sync(0xffffffffu, ref_max, o));
+  }
+  __shared__ float red[2][4];
+  if (lane == 0) {
+    red[0][warp] = err;
+    red[1][warp] = ref_max;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float e = 0.f, m = 0.f;
+    for (int w = 0; w < 4; ++w) {
+      e = fmaxf(e, red[0][w]);
+      m = fmaxf(m, red[1][w]);
+    }
+    out[0] = m > 0.f ? e / m : e;
+    out[1] = *s_ok ? 1.f : 0.f;
+  }
+}
+
+}  // namespace stag

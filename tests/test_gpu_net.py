@@ -69,7 +69,18 @@ def small():
     h.free()
 
 
+def test_tensor_core_selftest():
+    """One tile of tcgen05 products (values exact in bfloat16 and FP32)
+    against the CUDA cores: the descriptors, the accumulation over nine
+    steps and the tensor-memory read-back must reproduce the sums exactly."""
+    assert _stag().stag_tc_selftest() == 0.0
+
+
 def test_forward_matches_oracle(small):
+    """The 16 -> 16 layers mix channels on the tensor cores from bfloat16
+    hi + lo parts of the FP32 transports (16 significant bits, error <= 2^-18
+    of each value), the other layers in FP32: 5e-5 relative L2 over four
+    layers."""
     stag = _stag()
     dims, fat, lng, thin, h, net = small
     r = synth.random_spinor(dims, 51)
@@ -77,7 +88,9 @@ def test_forward_matches_oracle(small):
     stag.stag_net_apply(net, h, z, dev(r))
     params = _oracle_params(stag.stag_net_get_params(net, rounded=True), CH)
     zo, _ = onet.forward(fat, params, r, dims, oracle.parity_sites(dims, 0))
-    assert rel_l2(z.cpu().numpy(), zo) < 2e-5
+    err = rel_l2(z.cpu().numpy(), zo)
+    print(f"network forward rel. L2 error vs FP64 oracle: {err:.2e}")
+    assert err < 5e-5
 
 
 @pytest.mark.parametrize("kind", ["error", "residual"])
@@ -95,6 +108,7 @@ def test_gradient_matches_oracle(small, kind):
     else:
         lo, go = onet.backward_residual(fat, lng, params, r, mass, dims, even)
     go = _flat_grads(go)
+    print(f"{kind} loss rel. error {abs(loss - lo) / abs(lo):.2e}, gradient {np.linalg.norm(g - go) / np.linalg.norm(go):.2e}")
     assert abs(loss - lo) < 1e-5 * abs(lo)
     assert np.linalg.norm(g - go) / np.linalg.norm(go) < 1e-4
 
@@ -152,7 +166,7 @@ def trained():
         srcs = [dev(synth.gaussian_source(dims, 7000 + 10 * j + s)) for s in range(2)]
         pairs += make_pairs(h, srcs, mass, iters=[1, 3, 6, 10, 15, 22, 30, 40])
     net = stag.stag_net_create(CH, seed=5)
-    losses = stag.stag_net_train(net, pairs, epochs=6, batch=4, lr=2e-3, seed=2, loss="residual", mass=mass)
+    losses = stag.stag_net_train(net, pairs, epochs=16, batch=4, lr=2e-3, seed=2, loss="residual", mass=mass)
     yield dims, mass, net, losses, len(pairs)
     net.free()
     for h in handles:
@@ -182,13 +196,17 @@ def test_learned_fcg_converges_and_gains(trained):
     info = stag.stag_cg(h, x, bd, mass, mode="learned", precond=net, tol=1e-10)
     res = oracle.true_residual(fat, lng, x.cpu().numpy(), b, mass, dims)
     assert info["converged"] and res <= 1e-10 and info["precond_fallback"] == 0, (info, res)
-    # the same solver with the untrained network needs more iterations
+    # the same solver with the untrained network, and CG without a network,
+    # both need more iterations
     raw = stag.stag_net_create(CH, seed=5)
     x2 = torch.zeros_like(bd)
     info_raw = stag.stag_cg(h, x2, bd, mass, mode="learned", precond=raw, tol=1e-10)
     assert info_raw["converged"]
-    print(f"learned FCG iterations: trained {info['iters']}, untrained {info_raw['iters']}")
+    x3 = torch.zeros_like(bd)
+    info_cg = stag.stag_cg(h, x3, bd, mass, mode="mixed32", tol=1e-10)
+    print(f"learned FCG iterations: trained {info['iters']}, untrained {info_raw['iters']}, CG {info_cg['iters']}")
     assert info["iters"] < info_raw["iters"]
+    assert info["iters"] < 0.9 * info_cg["iters"]
     raw.free()
     h.free()
 
