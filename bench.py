@@ -572,8 +572,8 @@ def run_config(args):
         for it in items:
             it[0].free()
     elif args.config == "netpass":
-        # one network forward (z = N(r)) and one loss-and-gradient pass on 32^4
-        dims = (32, 32, 32, 32)
+        # one network forward (z = N(r)) and one loss-and-gradient pass (32^4 by default)
+        dims = (args.net_dims,) * 4
         fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
         h = stag.stag_load_links(dims, torch.from_numpy(fat).to(dev), torch.from_numpy(lng).to(dev), recon_long=12,
                                  prec_mask=0b0010)
@@ -597,7 +597,7 @@ def run_config(args):
         for l in range(4):
             # per site: 8 transports (66 flop) per input channel + 9 x Cin x Cout real-by-complex-3 mixes (12 flop)
             flops_fw += 2 * h.Vh * (8 * ch[l] * 66 + 9 * ch[l] * ch[l + 1] * 12)
-        print(json.dumps({"config": "network 1-16-16-16-1 on 32^4", "forward_s": t_f, "loss_grad_s": t_b,
+        print(json.dumps({"config": f"network 1-16-16-16-1 on {args.net_dims}^4", "forward_s": t_f, "loss_grad_s": t_b,
                           "forward_gflops": flops_fw / t_f / 1e9,
                           "families_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in fam.items()}}), flush=True)
         net.free()
@@ -687,6 +687,7 @@ def main(argv=None):
     ap.add_argument("--sweep-recons", nargs="+", type=int, default=[18, 12])
     ap.add_argument("--sweep-reps", type=int, default=20)
     ap.add_argument("--sweep-nrhs", nargs="+", type=int, default=[1])
+    ap.add_argument("--net-dims", type=int, default=32, help="lattice extent of the netpass config")
     ap.add_argument("--config", default="headline",
                     choices=["headline", "small", "multishift", "batch", "learned", "netpass"])
     ap.add_argument("--learned-pairs", type=int, default=2000)

@@ -187,6 +187,7 @@ struct NetRun {
   NetGeom ng;
   int Vh;
   std::vector<float2*> h, pre;  // per layer output (h[0] = input)
+  float2* U = nullptr;          // [9][2 Vh][3]: per-direction mixes of the one-channel output layer
   float2* g0 = nullptr;         // gradient buffers (ping-pong)
   float2* g1 = nullptr;
   float* part = nullptr;        // per-block partial sums for dW / db
@@ -217,6 +218,7 @@ static int net_run_init(stag_net_s* net, stag_lattice_s* lat, NetRun& R, bool tr
   }
   int cmax = 1;
   for (int l = 0; l <= net->nl; ++l) cmax = net->ch[l] > cmax ? net->ch[l] : cmax;
+  R.U = (float2*)net->ws.get(pre + "U", sites * NET_NDIR * 3 * sizeof(float2), &s);
   if (training) {
     R.g0 = (float2*)net->ws.get(pre + "g0", sites * cmax * 3 * sizeof(float2), &s);
     R.g1 = (float2*)net->ws.get(pre + "g1", sites * cmax * 3 * sizeof(float2), &s);
@@ -235,16 +237,33 @@ static void launch_layer(const NetRun& R, int l, const float2* in, float2* pre, 
   count_launch();
   if constexpr (CIN == 16 && COUT == 16) {
     // the channel mixing of a 16 -> 16 layer runs on the tensor cores
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_net_layer_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-      cudaFuncSetAttribute(k_net_layer_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-      attr = true;
+    // one CTA per 64-site tile
+    static bool attr[2] = {false, false};
+    if (!attr[GATE]) {
+      cudaFuncSetAttribute(k_net_layer_tc<GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+      attr[GATE] = true;
     }
     const int tiles = 2 * ((R.Vh + tc::TILE - 1) / tc::TILE);
     k_net_layer_tc<GATE><<<tiles, 128, tc::SMEM_BYTES, st>>>(R.ng, in, pre, out, W, b, transpose);
+  } else if constexpr (COUT == 1 && CIN == 16 && !GATE) {
+    if (!transpose) {
+      // one output channel: site-local mix into the nine directions, then
+      // one transport per direction
+      k_net_mix_local<CIN><<<grid_for(n, 256), 256, 0, st>>>(n, in, W, R.U);
+      count_launch();
+      k_net_transport_sum<<<grid_for(n, 256), 256, 0, st>>>(R.ng, R.U, out);
+    } else {
+      k_net_layer<CIN, COUT, GATE><<<(n + 127) / 128, 128, 0, st>>>(R.ng, in, pre, out, W, b, transpose);
+    }
   } else {
-    k_net_layer<CIN, COUT, GATE><<<(n + 127) / 128, 128, 0, st>>>(R.ng, in, pre, out, W, b, transpose);
+    // 16 output channels: the block's outputs are staged in shared memory
+    const size_t smem = COUT == 16 ? (size_t)128 * 97 * sizeof(float) : 0;
+    static bool attr = false;
+    if (COUT == 16 && !attr) {
+      cudaFuncSetAttribute(k_net_layer<CIN, COUT, GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    k_net_layer<CIN, COUT, GATE><<<(n + 127) / 128, 128, smem, st>>>(R.ng, in, pre, out, W, b, transpose);
   }
 }
 

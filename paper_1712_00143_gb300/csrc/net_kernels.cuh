@@ -89,15 +89,15 @@ __global__ void __launch_bounds__(128) k_net_layer(NetGeom ng, const float2* __r
   __syncthreads();
   const int Vh = ng.g.Vh;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 2 * Vh) return;
-  const int p = idx / Vh, s = idx - p * Vh;
+  const bool valid = idx < 2 * Vh;
+  const int p = valid ? idx / Vh : 0, s = valid ? idx - p * Vh : 0;
   float2 acc[COUT][3];
 #pragma unroll
   for (int c = 0; c < COUT; ++c)
 #pragma unroll
     for (int i = 0; i < 3; ++i) acc[c][i] = make_float2(0.f, 0.f);
 #pragma unroll 1
-  for (int d = 0; d < NET_NDIR; ++d) {
+  for (int d = 0; d < (valid ? NET_NDIR : 0); ++d) {
     int np, ns;
     net_neighbour(ng, p, s, d, np, ns);
     float2 w[9];
@@ -128,8 +128,7 @@ __global__ void __launch_bounds__(128) k_net_layer(NetGeom ng, const float2* __r
           acc[0][i].y += m[i].y;
         }
       }
-      continue;
-    }
+    } else {
 #pragma unroll 4
     for (int cp = 0; cp < CIN; ++cp) {
       float2 v[3], t[3];
@@ -157,7 +156,47 @@ __global__ void __launch_bounds__(128) k_net_layer(NetGeom ng, const float2* __r
         }
       }
     }
+    }
   }
+  if constexpr (COUT == 16) {
+    // staged epilogue: the block's 128 sites x 16 channels go through shared
+    // memory so that consecutive threads store consecutive 24-byte channel
+    // vectors (a site's record is 384 bytes; per-site stores would be strided)
+    extern __shared__ float net_epi[];  // [blockDim][97]
+    float* e = net_epi + threadIdx.x * 97;
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        e[c * 6 + 2 * i] = acc[c][i].x;
+        e[c * 6 + 2 * i + 1] = acc[c][i].y;
+      }
+    __syncthreads();
+    const int base = blockIdx.x * blockDim.x;
+    for (int q = threadIdx.x; q < (int)blockDim.x * 16; q += blockDim.x) {
+      const int sl = q >> 4, c = q & 15, site = base + sl;
+      if (site >= 2 * Vh) continue;
+      const float* ev = net_epi + sl * 97 + c * 6;
+      float2 v[3] = {make_float2(ev[0], ev[1]), make_float2(ev[2], ev[3]), make_float2(ev[4], ev[5])};
+      float2* ho = hout + ((size_t)site * 16 + c) * 3;
+      if (GATE) {
+        const float n2 = v[0].x * v[0].x + v[0].y * v[0].y + v[1].x * v[1].x + v[1].y * v[1].y + v[2].x * v[2].x +
+                         v[2].y * v[2].y;
+        const float sg = 1.f / (1.f + __expf(-(n2 - bias[c])));
+        float2* po = pre + ((size_t)site * 16 + c) * 3;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          po[i] = v[i];
+          ho[i] = make_float2(v[i].x * sg, v[i].y * sg);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) ho[i] = v[i];
+      }
+    }
+    return;
+  }
+  if (!valid) return;
   float2* po = act_ptr(pre, COUT, Vh, p, s);
   float2* ho = act_ptr(hout, COUT, Vh, p, s);
 #pragma unroll
@@ -180,47 +219,114 @@ __global__ void __launch_bounds__(128) k_net_layer(NetGeom ng, const float2* __r
 }
 
 // Gate backward: G_pre = s G_out + 2 s(1-s) Re<G_out, pre> pre  (in place on g)
-// and per-block partial sums of db_c = -sum s(1-s) Re<G_out, pre>.
+// and per-block partial sums of db_c = -sum s(1-s) Re<G_out, pre>.  One
+// thread per (site, channel): consecutive threads read and write consecutive
+// 24-byte channel vectors; a thread's channel stays fixed over the
+// grid-stride loop (the stride is a multiple of C).
 template <int C>
 __global__ void __launch_bounds__(256) k_net_gate_bwd(int n2vh, const float2* __restrict__ pre, float2* g,
                                                      const float* __restrict__ bias, float* __restrict__ db_part) {
-  __shared__ float sdb[C][8];
-  float db[C];
+  static_assert(C == 16, "one warp covers two sites of 16 channels");
+  __shared__ float sdb[8][C];
+  const int stride = gridDim.x * blockDim.x;
+  const int q0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = q0 & (C - 1);
+  const float bc = bias[c];
+  float db = 0.f;
+  for (int q = q0; q < n2vh * C; q += stride) {
+    const float2* pv = pre + (size_t)q * 3;
+    float2* gv = g + (size_t)q * 3;
+    float2 v[3], o[3];
+    float n2 = 0.f, pr = 0.f;
 #pragma unroll
-  for (int c = 0; c < C; ++c) db[c] = 0.f;
-  for (int site = blockIdx.x * blockDim.x + threadIdx.x; site < n2vh; site += gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const float2* pv = pre + ((size_t)site * C + c) * 3;
-      float2* gv = g + ((size_t)site * C + c) * 3;
-      float2 v[3], o[3];
-      float n2 = 0.f, pr = 0.f;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        v[i] = pv[i];
-        o[i] = gv[i];
-        n2 += v[i].x * v[i].x + v[i].y * v[i].y;
-        pr += o[i].x * v[i].x + o[i].y * v[i].y;
-      }
-      const float s = 1.f / (1.f + __expf(-(n2 - bias[c])));
-      const float sp = s * (1.f - s);
-      db[c] -= sp * pr;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) gv[i] = make_float2(s * o[i].x + 2.f * sp * pr * v[i].x, s * o[i].y + 2.f * sp * pr * v[i].y);
+    for (int i = 0; i < 3; ++i) {
+      v[i] = pv[i];
+      o[i] = gv[i];
+      n2 += v[i].x * v[i].x + v[i].y * v[i].y;
+      pr += o[i].x * v[i].x + o[i].y * v[i].y;
     }
-  }
-  // block sum per channel (fixed order): warp shuffle, then warps in order
+    const float sg = 1.f / (1.f + __expf(-(n2 - bc)));
+    const float sp = sg * (1.f - sg);
+    db -= sp * pr;
 #pragma unroll
-  for (int c = 0; c < C; ++c) {
-    float v = db[c];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sdb[c][threadIdx.x >> 5] = v;
+    for (int i = 0; i < 3; ++i)
+      gv[i] = make_float2(sg * o[i].x + 2.f * sp * pr * v[i].x, sg * o[i].y + 2.f * sp * pr * v[i].y);
   }
+  // lanes l and l + 16 hold the same channel; then warps in order
+  db += __shfl_xor_sync(0xffffffffu, db, 16);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane < C) sdb[warp][lane] = db;
   __syncthreads();
   if (threadIdx.x < C) {
     float v = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sdb[threadIdx.x][w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sdb[w][threadIdx.x];
     db_part[(size_t)blockIdx.x * C + threadIdx.x] = v;
+  }
+}
+
+// Output layer with one channel, mix first: u_d(y) = sum_c' W[d][0][c'] h_c'(y)
+// for the nine directions at every site (site-local, read once), then
+// (see k_net_transport_sum) out(x) = sum_d (T_d u_d)(x).  U: [9][2 Vh][3].
+template <int CIN>
+__global__ void __launch_bounds__(256) k_net_mix_local(int n2vh, const float2* __restrict__ hin,
+                                                      const __nv_bfloat16* __restrict__ W, float2* __restrict__ U) {
+  __shared__ float sw[NET_NDIR * CIN];
+  for (int i = threadIdx.x; i < NET_NDIR * CIN; i += blockDim.x) sw[i] = __bfloat162float(W[i]);
+  __syncthreads();
+  for (int site = blockIdx.x * blockDim.x + threadIdx.x; site < n2vh; site += gridDim.x * blockDim.x) {
+    float2 u[NET_NDIR][3];
+#pragma unroll
+    for (int d = 0; d < NET_NDIR; ++d)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[d][i] = make_float2(0.f, 0.f);
+    const float4* src = (const float4*)(hin + (size_t)site * CIN * 3);
+#pragma unroll
+    for (int k = 0; k < CIN * 3 / 2; ++k) {  // float4 k holds entries 2k, 2k + 1 (channel e / 3, colour e % 3)
+      const float4 f = __ldg(src + k);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = 2 * k + h, cp = e / 3, i = e - 3 * cp;
+        const float vx = h ? f.z : f.x, vy = h ? f.w : f.y;
+#pragma unroll
+        for (int d = 0; d < NET_NDIR; ++d) {
+          const float w = sw[d * CIN + cp];
+          u[d][i].x = fmaf(w, vx, u[d][i].x);
+          u[d][i].y = fmaf(w, vy, u[d][i].y);
+        }
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < NET_NDIR; ++d)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) U[((size_t)d * n2vh + site) * 3 + i] = u[d][i];
+  }
+}
+
+// out(x) = u_0(x) + sum_{d >= 1} hop_d(x) u_d(neighbour_d(x)).
+__global__ void __launch_bounds__(256) k_net_transport_sum(NetGeom ng, const float2* __restrict__ U,
+                                                          float2* __restrict__ hout) {
+  const int Vh = ng.g.Vh, n2 = 2 * Vh;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n2; idx += gridDim.x * blockDim.x) {
+    const int p = idx / Vh, s = idx - p * Vh;
+    float2 acc[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) acc[i] = __ldg(U + (size_t)idx * 3 + i);
+#pragma unroll 1
+    for (int d = 1; d < NET_NDIR; ++d) {
+      int np, ns;
+      net_neighbour(ng, p, s, d, np, ns);
+      float2 w[9], v[3];
+      load_hop_matrix(ng, p, s, d, w);
+      const float2* src = U + ((size_t)d * n2 + (size_t)np * Vh + ns) * 3;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) v[j] = __ldg(src + j);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) cmac(acc[i], w[3 * i + j], v[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) hout[(size_t)idx * 3 + i] = acc[i];
   }
 }
 

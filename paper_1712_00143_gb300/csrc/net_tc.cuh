@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(128, 4)
   const int s = s0 + s_local;
   const bool valid = s < Vh;
   const uint32_t a_base = smem_u32(A);
+  const Coord crd = valid ? cb_coords(ng.g, s, p) : Coord{0, 0, 0, 0};  // once, not per direction
 
 #pragma unroll 1
   for (int d = 0; d < NET_NDIR; ++d) {
@@ -219,9 +220,12 @@ __global__ void __launch_bounds__(128, 4)
     float2 w[9];
     const float2* src = nullptr;
     if (valid) {
-      int np, ns;
-      net_neighbour(ng, p, s, d, np, ns);
-      if (d) load_hop_matrix(ng, p, s, d, w);
+      int np = p, ns = s;
+      if (d) {
+        ns = cb_neighbour(ng.g, s, crd, (d - 1) >> 1, (d & 1) ? 1 : -1);
+        np = 1 - p;
+        load_hop_matrix(ng, p, s, d, w);
+      }
       src = act_ptr(hin, 16, Vh, np, ns) + half * 24;
     }
 #pragma unroll
