@@ -19,7 +19,26 @@ struct Geom {
   int Lxh;   // Lx / 2
   int Vh;    // sites per parity
   int sy, sz, st;  // checkerboard strides of y, z, t
+  // exact division by Lxh, Ly, Lz as a multiply and a shift:
+  // n / d = (n * m) >> s for 0 <= n <= 2^30 (see magic_div)
+  unsigned long long m_xh, m_y, m_z;
+  int s_xh, s_y, s_z;
 };
+
+// Multiplier and shift for division by d >= 1: with l = ceil(log2 d),
+// s = 31 + l and m = ceil(2^s / d), m d = 2^s + e (0 <= e < d), so
+// n m / 2^s = n / d + n e / (d 2^s) and the second term is below 1/d for
+// n < 2^31: the floor is exact.  n m < 2^30 (2^32 + 1) fits in 64 bits.
+__host__ __device__ inline void magic_div(int d, unsigned long long& m, int& s) {
+  int l = 0;
+  while ((1 << l) < d) ++l;
+  s = 31 + l;
+  m = ((1ull << s) + (unsigned long long)d - 1) / (unsigned long long)d;
+}
+
+__host__ __device__ __forceinline__ int mdiv(int n, unsigned long long m, int s) {
+  return (int)(((unsigned long long)(unsigned)n * m) >> s);
+}
 
 struct Coord {
   int x, y, z, t;
@@ -33,17 +52,20 @@ __host__ __device__ inline Geom make_geom(const int d[4]) {
   g.sz = g.Lxh * d[1];
   g.st = g.Lxh * d[1] * d[2];
   g.Vh = g.st * d[3];
+  magic_div(g.Lxh, g.m_xh, g.s_xh);
+  magic_div(d[1], g.m_y, g.s_y);
+  magic_div(d[2], g.m_z, g.s_z);
   return g;
 }
 
 __device__ __forceinline__ Coord cb_coords(const Geom& g, int s, int parity) {
-  int xh = s % g.Lxh;
-  int r = s / g.Lxh;
+  const int q1 = mdiv(s, g.m_xh, g.s_xh);  // s / Lxh
+  const int xh = s - q1 * g.Lxh;
+  const int q2 = mdiv(q1, g.m_y, g.s_y);   // / Ly
   Coord c;
-  c.y = r % g.L[1];
-  r /= g.L[1];
-  c.z = r % g.L[2];
-  c.t = r / g.L[2];
+  c.y = q1 - q2 * g.L[1];
+  c.t = mdiv(q2, g.m_z, g.s_z);            // / Lz
+  c.z = q2 - c.t * g.L[2];
   c.x = 2 * xh + ((parity + c.y + c.z + c.t) & 1);
   return c;
 }

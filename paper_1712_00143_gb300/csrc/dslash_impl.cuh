@@ -68,14 +68,14 @@ __device__ __forceinline__ void hop_recon12(A2 acc[3], const uint4 (&buf)[NCH], 
     A2 r2;
     r2.x = m[k].x * m[3 + l].x - m[k].y * m[3 + l].y - (m[l].x * m[3 + k].x - m[l].y * m[3 + k].y);
     r2.y = -(m[k].x * m[3 + l].y + m[k].y * m[3 + l].x - (m[l].x * m[3 + k].y + m[l].y * m[3 + k].x));
-    if (P == 15) {
-      // rows hold integers 32767 * entry: row 2 comes out 32767 times too large
-      r2.x *= 1.0f / FX_ONE;
-      r2.y *= 1.0f / FX_ONE;
-    }
     cmac(t[0], m[j], psi[j]);
     cmac(t[1], m[3 + j], psi[j]);
     cmac(t[2], r2, psi[j]);
+  }
+  if (P == 15) {
+    // rows hold integers 32767 * entry: row 2 (and so t[2]) comes out 32767 times too large
+    t[2].x *= 1.0f / FX_ONE;
+    t[2].y *= 1.0f / FX_ONE;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
