@@ -22,6 +22,10 @@ Parity status of each function (what pins it, checked by the CPU tests):
   * apply_m_at_sites       -- equals apply_m restricted to the sampled sites
                               (checked on small lattices), used to check
                               full-size GPU results site by site.
+  * links (module)         -- fat and Naik links from thin links: unit-link
+                              closed form, single-link insertion at the sites
+                              the definition names, gauge covariance
+                              (tests/test_links_oracle.py).
 """
 
 from .staggered import (
