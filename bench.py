@@ -495,7 +495,8 @@ def run_config(args):
     `batch` 12 lattices x 8 right-hand sides in one batched call vs one
     stag_cg per system; `learned` training and evaluating the network
     preconditioner on 32^4; `netpass` one network forward and one
-    loss-and-gradient pass on 32^4."""
+    loss-and-gradient pass on 32^4; `links` fat and Naik links built from
+    thin links on the GPU."""
     import torch
 
     import paper_1712_00143_gb300 as stag
@@ -602,6 +603,48 @@ def run_config(args):
                           "families_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in fam.items()}}), flush=True)
         net.free()
         h.free()
+    elif args.config == "links":
+        # fat and Naik links from thin links on the GPU (FP64), 32^4 and 48^3 x 96
+        import oracle.links as olk
+
+        from synth.gauge import Lattice, thin_links
+
+        # per (site, direction): 6 staples x 2 complex 3x3 products + 2 Naik products,
+        # 216 flop each (27 complex FMA), plus the combination: about 3080 flop
+        flop_per_link = 14 * 216 + 36 + 18
+        rows = {}
+        for dims in ((32, 32, 32, 32), (48, 48, 48, 96)):
+            lat = Lattice(dims)
+            thin = thin_links(lat, EPS, GAUGE_SEED).reshape(lat.V, 4, 3, 3).to(dev)
+            fat, lng = stag.stag_build_links(dims, thin)
+            torch.cuda.synchronize()
+            stag.stag_profile_reset()
+            stag.stag_profile_select("links", 1)
+            stag.stag_profile_enable(True)
+            wall, _ = _timed(lambda: stag.stag_build_links(dims, thin, fat, lng), reps=5)
+            n, ms = stag.stag_profile_read("links")
+            stag.stag_profile_enable(False)
+            stag.stag_profile_select("", 1)
+            per = ms / max(n, 1) * 1e-3
+            tf = 4 * lat.V * flop_per_link / per / 1e12
+            rows["x".join(map(str, dims))] = {"device_s": per, "wall_s": wall, "fp64_tflops": tf}
+            del thin, fat, lng
+            torch.cuda.empty_cache()
+        # the oracle on a 16^4 sample (numpy, one core), scaled per site
+        d16 = (16, 16, 16, 16)
+        lat = Lattice(d16)
+        t16 = thin_links(lat, EPS, GAUGE_SEED).reshape(lat.V, 4, 3, 3).numpy()
+        t0 = time.perf_counter()
+        olk.fat_links(t16, d16)
+        olk.naik_links(t16, d16)
+        per_site = (time.perf_counter() - t0) / lat.V
+        print(json.dumps({"config": "link construction (3-staple fat + Naik) from thin links, FP64",
+                          "unit": "s", "results": rows,
+                          "roofline": {"bound": "fp64_alu", "flop_per_link": flop_per_link,
+                                       "note": "FP64 peak about 1.2 TFLOP/s on GB300 (measured DGEMM 1.10)"},
+                          "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "16^4, scaled per site",
+                                           "s_per_site": per_site,
+                                           "value_32_4": per_site * 32 ** 4}}), flush=True)
     elif args.config == "learned":
         # 32^4, m = 0.01: 2000 (residual, error) pairs from the unpreconditioned
         # mixed CG on 24 training fields, network 1-16-16-16-1 trained on the
@@ -689,7 +732,7 @@ def main(argv=None):
     ap.add_argument("--sweep-nrhs", nargs="+", type=int, default=[1])
     ap.add_argument("--net-dims", type=int, default=32, help="lattice extent of the netpass config")
     ap.add_argument("--config", default="headline",
-                    choices=["headline", "small", "multishift", "batch", "learned", "netpass"])
+                    choices=["headline", "small", "multishift", "batch", "learned", "netpass", "links"])
     ap.add_argument("--learned-pairs", type=int, default=2000)
     ap.add_argument("--learned-fields", type=int, default=24)
     ap.add_argument("--learned-epochs", type=int, default=2)

@@ -285,6 +285,20 @@ int stag_net_loss_grad(stag_net_t net, stag_lattice_t lat, const void* r, const 
 int stag_net_train(stag_net_t net, const stag_train_pair* pairs, int npairs, const stag_train_params* tp,
                    double* losses, void* stream);
 
+/* Link construction before the operator (the paper's production code smears
+ * the thin links before the solver: HISQ-link smearing, Sec. 1 and Sec. 2,
+ * Fig. 1; the workload uses the three-staple fat link and the Naik link):
+ *   F_mu(x) = c1 U_mu(x) + c_staple sum_{nu != mu} [ U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+ *                                                   + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) ]
+ *   L_mu(x) = c3 U_mu(x) U_mu(x+mu) U_mu(x+2mu)
+ * (the benchmark workload: c1 = 1, c_staple = 1/8, c3 = -1/24), in FP64 on
+ * the GPU, periodic boundaries, no staggered phases (stag_load_links folds
+ * them in).  thin, fat, lng: device, canonical [V][4][3][3] complex double,
+ * caller-owned; fat and lng must not overlap thin or each other
+ * (STAG_EINVAL).  dims: even extents >= 4.  Asynchronous on `stream`. */
+int stag_build_links(const int dims[4], const void* thin, void* fat, void* lng, double c1, double c_staple,
+                     double c3, void* stream);
+
 /* Check of this build's tensor-core path on the current GPU (the path the
  * network's 16 -> 16 layers take): one tile of tcgen05 bfloat16 products
  * with FP32 accumulation in tensor memory, 9 accumulated steps, compared

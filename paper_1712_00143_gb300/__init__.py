@@ -64,6 +64,7 @@ EXPORTS = (
     "stag_net_loss_grad",
     "stag_net_train",
     "stag_tc_selftest",
+    "stag_build_links",
     "stag_strerror",
     "stag_profile_enable",
     "stag_profile_select",
@@ -180,6 +181,7 @@ def load_library(path=LIB_PATH):
         ),
         "stag_net_train": (ci, [vp, ctypes.POINTER(TrainPair), ci, ctypes.POINTER(TrainParams), ctypes.POINTER(cd), vp]),
         "stag_tc_selftest": (ci, [ctypes.POINTER(cd)]),
+        "stag_build_links": (ci, [ctypes.POINTER(ci), vp, vp, vp, cd, cd, cd, vp]),
         "stag_strerror": (ctypes.c_char_p, [ci]),
         "stag_profile_enable": (ci, [ci]),
         "stag_profile_select": (ci, [ctypes.c_char_p, ci]),
@@ -482,6 +484,20 @@ def stag_net_train(net, pairs, epochs=1, batch=4, lr=1e-3, seed=1, loss="residua
         "stag_net_train",
     )
     return losses
+
+
+def stag_build_links(dims, thin, fat=None, lng=None, c1=1.0, c_staple=0.125, c3=-1.0 / 24.0, stream=None):
+    """Fat and Naik links from thin links on the GPU (FP64).  thin: contiguous
+    complex128 CUDA tensor of V*4*9 entries (canonical [V][4][3][3]); fat and
+    lng are allocated like thin when not given.  Returns (fat, lng)."""
+    V = int(dims[0]) * int(dims[1]) * int(dims[2]) * int(dims[3])
+    n = V * 36
+    fat = torch.empty_like(thin) if fat is None else fat
+    lng = torch.empty_like(thin) if lng is None else lng
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    _check(_lib.stag_build_links(d, _ptr(thin, "thin", n), _ptr(fat, "fat", n), _ptr(lng, "lng", n),
+                                 float(c1), float(c_staple), float(c3), _stream(stream)), "stag_build_links")
+    return fat, lng
 
 
 def stag_tc_selftest():
