@@ -496,7 +496,7 @@ def run_config(args):
     stag_cg per system; `learned` training and evaluating the network
     preconditioner on 32^4; `netpass` one network forward and one
     loss-and-gradient pass on 32^4; `links` fat and Naik links built from
-    thin links on the GPU."""
+    thin links on the GPU; `gaugeforce` the Symanzik one-loop gauge force."""
     import torch
 
     import paper_1712_00143_gb300 as stag
@@ -645,6 +645,52 @@ def run_config(args):
                           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "16^4, scaled per site",
                                            "s_per_site": per_site,
                                            "value_32_4": per_site * 32 ** 4}}), flush=True)
+    elif args.config == "gaugeforce":
+        # Symanzik one-loop gauge force (FP64) on 24^4 (the paper's per-node weak-scaling
+        # volume, Fig. 7) and 32^4
+        import oracle.gauge_force as ogf
+
+        from synth.gauge import Lattice, thin_links
+
+        beta = 6.0
+        coef = ogf.luscher_weisz_coefficients(0.87)
+        # per link: 6 plaquette staples x 2 products + 42 five-link staples x 4
+        # products (216 flop each), 48 coefficient updates (36 flop), U Sigma and TA
+        flop_per_link = (6 * 2 + 42 * 4 + 1) * 216 + 48 * 36 + 60
+        rows = {}
+        for dims in ((24, 24, 24, 24), (32, 32, 32, 32)):
+            lat = Lattice(dims)
+            thin = thin_links(lat, EPS, GAUGE_SEED).reshape(lat.V, 4, 3, 3).to(dev)
+            F = stag.stag_gauge_force(dims, thin, beta, *coef)
+            torch.cuda.synchronize()
+            stag.stag_profile_reset()
+            stag.stag_profile_select("gauge_force", 1)
+            stag.stag_profile_enable(True)
+            wall, _ = _timed(lambda: stag.stag_gauge_force(dims, thin, beta, *coef, force=F), reps=3)
+            n, ms = stag.stag_profile_read("gauge_force")
+            stag.stag_profile_enable(False)
+            stag.stag_profile_select("", 1)
+            per = ms / max(n, 1) * 1e-3
+            rows["x".join(map(str, dims))] = {"device_s": per, "wall_s": wall,
+                                              "fp64_tflops": 4 * lat.V * flop_per_link / per / 1e12,
+                                              "gflops_per_site": 4 * flop_per_link / 1e9}
+            del thin, F
+            torch.cuda.empty_cache()
+        # the oracle on a 4^4 x 6 sample (numpy, one core), scaled per link
+        d = (4, 4, 4, 6)
+        lat = Lattice(d)
+        ts = thin_links(lat, EPS, GAUGE_SEED).reshape(lat.V, 4, 3, 3).numpy()
+        t0 = time.perf_counter()
+        ogf.force(ts, d, beta, *coef)
+        per_link = (time.perf_counter() - t0) / (4 * lat.V)
+        print(json.dumps({"config": "Symanzik one-loop gauge force (plaquette, rectangle, parallelogram), FP64",
+                          "coefficients": {"beta": beta, "u0": 0.87, "c_pl": coef[0], "c_rt": coef[1], "c_pg": coef[2]},
+                          "unit": "s", "results": rows,
+                          "roofline": {"bound": "fp64_alu", "flop_per_link": flop_per_link,
+                                       "note": "FP64 peak about 1.2 TFLOP/s on GB300 (measured DGEMM 1.10)"},
+                          "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "4^4 x 6, scaled per link",
+                                           "s_per_link": per_link, "value_24_4": per_link * 4 * 24 ** 4}}),
+              flush=True)
     elif args.config == "learned":
         # 32^4, m = 0.01: 2000 (residual, error) pairs from the unpreconditioned
         # mixed CG on 24 training fields, network 1-16-16-16-1 trained on the
@@ -732,7 +778,8 @@ def main(argv=None):
     ap.add_argument("--sweep-nrhs", nargs="+", type=int, default=[1])
     ap.add_argument("--net-dims", type=int, default=32, help="lattice extent of the netpass config")
     ap.add_argument("--config", default="headline",
-                    choices=["headline", "small", "multishift", "batch", "learned", "netpass", "links"])
+                    choices=["headline", "small", "multishift", "batch", "learned", "netpass", "links",
+                             "gaugeforce"])
     ap.add_argument("--learned-pairs", type=int, default=2000)
     ap.add_argument("--learned-fields", type=int, default=24)
     ap.add_argument("--learned-epochs", type=int, default=2)

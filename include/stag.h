@@ -299,6 +299,22 @@ int stag_net_train(stag_net_t net, const stag_train_pair* pairs, int npairs, con
 int stag_build_links(const int dims[4], const void* thin, void* fat, void* lng, double c1, double c_staple,
                      double c3, void* stream);
 
+/* Symanzik one-loop improved gauge force (the paper's second benchmark
+ * routine, Sec. 4.2, Figs. 6-8; the paper gives no formula, this is the
+ * Luscher-Weisz form).  Action S = beta sum_loops c (1 - Re Tr W / 3) over
+ * plaquettes (c_pl), 1x2 rectangles (c_rt) and parallelograms a, b, c, -a,
+ * -b, -c over three directions (c_pg), each geometric loop once.  Output:
+ *   force[x][mu] = (beta/3) TA[U_mu(x) Sigma_mu(x)],
+ *   TA(M) = (M - M^dag)/2 - Tr(M - M^dag)/6,
+ * Sigma_mu(x) = sum over the 6 + 18 + 24 loops through U_mu(x) of c times
+ * the product of their other links (each loop traversing U_mu(x) forward),
+ * so that U_mu(x) -> exp(eps X) U_mu(x) changes S by -eps Re Tr(X force).
+ * FP64.  thin, force: device, canonical [V][4][3][3] complex double,
+ * caller-owned, not overlapping (STAG_EINVAL).  dims: even extents >= 4.
+ * Asynchronous on `stream`. */
+int stag_gauge_force(const int dims[4], const void* thin, void* force, double beta, double c_pl, double c_rt,
+                     double c_pg, void* stream);
+
 /* Check of this build's tensor-core path on the current GPU (the path the
  * network's 16 -> 16 layers take): one tile of tcgen05 bfloat16 products
  * with FP32 accumulation in tensor memory, 9 accumulated steps, compared

@@ -65,6 +65,7 @@ EXPORTS = (
     "stag_net_train",
     "stag_tc_selftest",
     "stag_build_links",
+    "stag_gauge_force",
     "stag_strerror",
     "stag_profile_enable",
     "stag_profile_select",
@@ -182,6 +183,7 @@ def load_library(path=LIB_PATH):
         "stag_net_train": (ci, [vp, ctypes.POINTER(TrainPair), ci, ctypes.POINTER(TrainParams), ctypes.POINTER(cd), vp]),
         "stag_tc_selftest": (ci, [ctypes.POINTER(cd)]),
         "stag_build_links": (ci, [ctypes.POINTER(ci), vp, vp, vp, cd, cd, cd, vp]),
+        "stag_gauge_force": (ci, [ctypes.POINTER(ci), vp, vp, cd, cd, cd, cd, vp]),
         "stag_strerror": (ctypes.c_char_p, [ci]),
         "stag_profile_enable": (ci, [ci]),
         "stag_profile_select": (ci, [ctypes.c_char_p, ci]),
@@ -498,6 +500,18 @@ def stag_build_links(dims, thin, fat=None, lng=None, c1=1.0, c_staple=0.125, c3=
     _check(_lib.stag_build_links(d, _ptr(thin, "thin", n), _ptr(fat, "fat", n), _ptr(lng, "lng", n),
                                  float(c1), float(c_staple), float(c3), _stream(stream)), "stag_build_links")
     return fat, lng
+
+
+def stag_gauge_force(dims, thin, beta, c_pl, c_rt, c_pg, force=None, stream=None):
+    """Symanzik one-loop gauge force (FP64) from thin links (contiguous complex128
+    CUDA tensor, canonical [V][4][3][3]); returns the force tensor, same layout."""
+    V = int(dims[0]) * int(dims[1]) * int(dims[2]) * int(dims[3])
+    n = V * 36
+    force = torch.empty_like(thin) if force is None else force
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    _check(_lib.stag_gauge_force(d, _ptr(thin, "thin", n), _ptr(force, "force", n), float(beta), float(c_pl),
+                                 float(c_rt), float(c_pg), _stream(stream)), "stag_gauge_force")
+    return force
 
 
 def stag_tc_selftest():
