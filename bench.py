@@ -5,12 +5,16 @@ equilibrated ensembles): 32^4 lattice, thin links exp(0.3 i H) reunitarised,
 fat = U + 1/8 staples, Naik = -1/24 UUU, periodic, m = 0.01, 4 seeded
 Gaussian even-site sources, FP64 true relative residual 1e-10.
 
-A step solves all 4 sources with the chosen solver (stag_cg through the C
-ABI, inputs resident in HBM).  `value` is seconds per source solve.  The
-same JSON line carries the plain FP64 CG time, the Dslash roofline (device
-time of the dominant kernel per launch, measured with CUDA events on its
-launch stream during the timed region), the end-to-end time with host
-buffers, the oracle's CPU time on a bounded sample, and the SM clocks seen.
+A step solves all 4 sources with the chosen solver: mixed-precision CG
+(FP32 sloppy operator and vectors, FP64 reliable updates) on the 4 sources
+at once, one stag_batch_solve call through the C ABI (every system its own
+CG and stopping point, one multi-right-hand-side Dslash per operator
+application), inputs resident in HBM.  `value` is seconds per source solve.
+The same JSON line carries the plain FP64 CG time (stag_cg per source), the
+Dslash roofline (device time of the dominant kernel per launch, measured
+with CUDA events on its launch stream during the timed region), the
+end-to-end time with host buffers, the oracle's CPU time on a bounded
+sample, and the SM clocks seen.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -36,7 +40,8 @@ NSRC = 4
 TOL = 1e-10
 GAUGE_SEED = 1000
 SOURCE_SEEDS = [5000 + k for k in range(NSRC)]
-CHOSEN = "mixedfx16"
+CHOSEN = "mixed32"
+BATCHED = True  # the 4 sources in one batched call (multi-right-hand-side operator)
 RECON = 12
 FLOP_PER_SITE = 1146
 # algorithmic bytes per output site of one Dslash: 16 link matrices (8 fat x
@@ -55,9 +60,12 @@ def dslash_bytes_per_site(prec, recon):
     return (8 * 9 + 8 * nl) * ELEM_BYTES[prec] + 2 * VEC_BYTES[prec]
 
 
-def kernel_source_hash():
+def kernel_source_hash(kernel_id="k_dslash"):
     h = hashlib.sha256()
-    for f in ("dslash_impl.cuh", "common.cuh", "links.cu"):
+    files = ("dslash_impl.cuh", "common.cuh", "links.cu")
+    if kernel_id.startswith("k_dslash_m"):
+        files = files + ("batch_kernels.cuh", "dslash_mrhs.cuh")
+    for f in files:
         with open(os.path.join(ROOT, "paper_1712_00143_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -82,7 +90,7 @@ def ncu_traffic(kernel_id):
     except (OSError, ValueError):
         return None
     ent = d.get(kernel_id)
-    if not ent or ent.get("source_hash") != kernel_source_hash():
+    if not ent or ent.get("source_hash") != kernel_source_hash(kernel_id):
         return None
     return ent.get("bytes_per_launch")
 
@@ -239,11 +247,18 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     Vh = h.Vh
 
+    B = torch.stack(bs).contiguous()
+    X = torch.zeros_like(B)
+
     def step(mode):
+        if BATCHED and mode == CHOSEN:
+            return stag.stag_batch_solve([(h, X, B, NSRC, MASS)], mode=mode, tol=TOL)
         infos = []
         for x, b in zip(xs, bs):
             infos.append(stag.stag_cg(h, x, b, MASS, mode=mode, tol=TOL))
         return infos
+
+    fam_plain, fam_epi = ("dslash_mrhs", "dslash_mrhs_epi") if BATCHED else ("dslash", "dslash_epi")
 
     # plain FP64 reference solve (one pass over the sources, after one warm-up)
     step("plain64")
@@ -260,7 +275,7 @@ def run_gpu(args, rank, world, local_rank):
     stag.stag_profile_reset()
     # event pairs around the two Dslash kernels only, one launch in 8 of each,
     # so that the timed steps carry little instrumentation
-    stag.stag_profile_select("dslash,dslash_epi", 8)
+    stag.stag_profile_select(f"{fam_plain},{fam_epi}", 8)
     stag.stag_profile_enable(True)
     launches0 = stag.stag_launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -279,8 +294,8 @@ def run_gpu(args, rank, world, local_rank):
         barrier(world)
     launches = stag.stag_launch_count() - launches0
     shapes = {k: stag.stag_tuned_shape(h, MODE_PREC[CHOSEN], i) for i, k in enumerate(("plain", "epilogue"))}
-    n_d, ms_d = stag.stag_profile_read("dslash")
-    n_e, ms_e = stag.stag_profile_read("dslash_epi")
+    n_d, ms_d = stag.stag_profile_read(fam_plain)
+    n_e, ms_e = stag.stag_profile_read(fam_epi)
     stag.stag_profile_enable(False)
     stag.stag_profile_select("", 1)
     ms_total = reduce_max(e0.elapsed_time(e1), world)
@@ -296,11 +311,18 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(max(1, min(args.steps, 3))):
-        for k in range(NSRC):
-            bd = hb[k].to(dev, non_blocking=True)
+        if BATCHED:
+            bd = torch.stack([t.to(dev, non_blocking=True) for t in hb]).contiguous()
             xd = torch.zeros_like(bd)
-            stag.stag_cg(h, xd, bd, MASS, mode=CHOSEN, tol=TOL)
-            hx[k].copy_(xd, non_blocking=True)
+            stag.stag_batch_solve([(h, xd, bd, NSRC, MASS)], mode=CHOSEN, tol=TOL)
+            for k in range(NSRC):
+                hx[k].copy_(xd[k], non_blocking=True)
+        else:
+            for k in range(NSRC):
+                bd = hb[k].to(dev, non_blocking=True)
+                xd = torch.zeros_like(bd)
+                stag.stag_cg(h, xd, bd, MASS, mode=CHOSEN, tol=TOL)
+                hx[k].copy_(xd, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = reduce_max((time.perf_counter() - t0) / max(1, min(args.steps, 3)) / NSRC, world)
     vec_bytes = Vh * 3 * 16
@@ -309,10 +331,20 @@ def run_gpu(args, rank, world, local_rank):
     ok = all(i["converged"] and i["true_rel_resid"] <= TOL for i in infos_all + plain_infos)
     prec = MODE_PREC[CHOSEN]
     per_launch_ms = ms_d / max(n_d, 1)
-    bytes_launch = dslash_bytes_per_site(prec, RECON) * Vh
+    pbits = {"fp32": 32, "fp16": 16, "fx16": 15, "fp64": 64}[prec]
+    nl = 6 if RECON == 12 else 9
+    if BATCHED:
+        # one launch: the links once and NSRC input and output vectors
+        bytes_launch = ((8 * 9 + 8 * nl) * ELEM_BYTES[prec] + 2 * NSRC * VEC_BYTES[prec]) * Vh
+        capped = prec == "fp32" and NSRC <= 4  # the register-capped variant (six blocks per SM)
+        kernel_id = f"k_dslash_m{'_cap' if capped else ''}<{pbits},{nl},{NSRC}>"
+        sites_launch = NSRC * Vh
+    else:
+        bytes_launch = dslash_bytes_per_site(prec, RECON) * Vh
+        kernel_id = f"k_dslash<{pbits},{nl}>"
+        sites_launch = Vh
     achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    kernel_id = f"k_dslash<{ {'fp32': 32, 'fp16': 16, 'fx16': 15, 'fp64': 64}[prec] },{6 if RECON == 12 else 9}>"
     traffic = ncu_traffic(kernel_id)
     iters = [i["iters"] for i in infos_all[:NSRC]]
     iters_plain = [i["iters"] for i in plain_infos]
@@ -339,7 +371,7 @@ def run_gpu(args, rank, world, local_rank):
             "config": {
                 "workload": "32^4 even-odd improved-staggered CG, m=0.01, eps=0.3, 4 Gaussian sources, "
                 "1e-10 FP64 true residual",
-                "solver": CHOSEN,
+                "solver": f"{CHOSEN}, {NSRC} sources batched (stag_batch_solve)" if BATCHED else CHOSEN,
                 "link_storage": f"{prec}, Naik recon {RECON}",
                 "sources_per_step": NSRC,
                 "l2": "inputs larger than L2 (links 0.5-1.2 GB per precision)",
@@ -362,9 +394,12 @@ def run_gpu(args, rank, world, local_rank):
                 "launches_timed": n_d,
                 "launches_sampled_every": 8,
                 "avg_launch_us": per_launch_ms * 1e3,
-                "gflops": FLOP_PER_SITE * Vh / (per_launch_ms * 1e-3) / 1e9,
+                "gflops": FLOP_PER_SITE * sites_launch / (per_launch_ms * 1e-3) / 1e9,
                 "epilogue_variant_avg_us": ms_e / max(n_e, 1) * 1e3,
-                "launch_shape": {k: {"block": v[0], "min_blocks_per_sm": v[1], "tuned_us": v[2]} for k, v in shapes.items()},
+                "launch_shape": ({"multi_rhs": {"block": 128, "sites_per_thread": 1, "rhs_per_thread": NSRC}}
+                                 if BATCHED else
+                                 {k: {"block": v[0], "min_blocks_per_sm": v[1], "tuned_us": v[2]}
+                                  for k, v in shapes.items()}),
             },
             "e2e": {
                 "value": e2e_s,
@@ -450,7 +485,7 @@ def run_dslash_sweep(args):
                     if nrhs > 1:
                         psi = psi.unsqueeze(0).repeat(nrhs, 1, 1).contiguous()
                     out = torch.empty_like(psi)
-                    fam = "dslash" if nrhs == 1 else "dslash_mrhs"
+                    fam = ("dslash" if nrhs == 1 else "dslash_mrhs") + ("64" if prec == "fp64" else "")
                     for _ in range(3):
                         stag.stag_dslash(h, out, psi, 1, prec, nrhs=nrhs)
                     torch.cuda.synchronize()

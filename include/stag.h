@@ -330,10 +330,14 @@ const char* stag_strerror(int status);
 /* ---------------------------------------------------------- instrumentation
  * When enabled, every kernel the library launches is bracketed by a pair of
  * CUDA events recorded on its launch stream; stag_profile_read returns, for
- * a kernel family name ("dslash", "dslash_epilogue", "blas", "reduce",
- * "convert", "links"), the number of launches and their summed device time
- * (ms).  stag_launch_count counts all library kernel launches since the last
- * reset, whether or not profiling is on. */
+ * a kernel family name, the number of launches and their summed device
+ * time (ms).  Families: "dslash", "dslash_epi" (FP32 and 16-bit operator,
+ * plain and with the fused axpy/reduction epilogue), "dslash64",
+ * "dslash64_epi" (FP64), "dslash_mrhs", "dslash_mrhs_epi", "dslash_mrhs64",
+ * "dslash_mrhs64_epi" (multi-right-hand-side forms), "blas", "reduce",
+ * "convert", "links", "net", "net_bwd", "gauge_force".  stag_launch_count
+ * counts all library kernel launches since the last reset, whether or not
+ * profiling is on. */
 int stag_profile_enable(int on);
 /* Restrict the event pairs to the listed families (comma-separated, e.g.
  * "dslash,dslash_epi"; NULL or "" times every family) and to one launch in

@@ -76,11 +76,19 @@ int mdslash(const stag_lattice_s* lat, SpinorM<P> out, SpinorM<P> in, int out_pa
   if (!L.present) return STAG_EINVAL;
   DslashArgsM<P> a = make_args_m<P>(lat, in, out_parity);
   const int G = (lat->g.Vh + MB - 1) / MB;
-  ProfScope ps("dslash_mrhs", st);
-  if (P == 64 || L.nl == 9)
-    k_dslash_m<P, 9, N><<<G, MB, 0, st>>>(a, out, flags);
-  else
-    k_dslash_m<P, (P == 64 ? 9 : 6), N><<<G, MB, 0, st>>>(a, out, flags);
+  ProfScope ps(P == 64 ? "dslash_mrhs64" : "dslash_mrhs", st);
+  constexpr int NL6 = P == 64 ? 9 : 6;
+  if constexpr (mrhs_capped(P, N)) {
+    if (L.nl == 9)
+      k_dslash_m_cap<P, 9, N><<<G, MB, 0, st>>>(a, out, flags);
+    else
+      k_dslash_m_cap<P, NL6, N><<<G, MB, 0, st>>>(a, out, flags);
+  } else {
+    if (P == 64 || L.nl == 9)
+      k_dslash_m<P, 9, N><<<G, MB, 0, st>>>(a, out, flags);
+    else
+      k_dslash_m<P, NL6, N><<<G, MB, 0, st>>>(a, out, flags);
+  }
   return last_launch_status();
 }
 
@@ -93,12 +101,20 @@ int mdslash_epi(const stag_lattice_s* lat, SpinorM<Acc<P>::value> out, SpinorM<P
   DslashArgsM<P> a = make_args_m<P>(lat, in, out_parity);
   const int G = (lat->g.Vh + MB - 1) / MB;
   if (RED && G > rs.max_grid) return STAG_EINVAL;
-  ProfScope ps("dslash_mrhs_epi", st);
+  ProfScope ps(P == 64 ? "dslash_mrhs64_epi" : "dslash_mrhs_epi", st);
   RedBuf rb{rs.partials, rs.counter};
-  if (P == 64 || L.nl == 9)
-    k_dslash_m_epi<P, 9, N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
-  else
-    k_dslash_m_epi<P, (P == 64 ? 9 : 6), N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
+  constexpr int NL6 = P == 64 ? 9 : 6;
+  if constexpr (mrhs_capped(P, N)) {
+    if (L.nl == 9)
+      k_dslash_m_epi_cap<P, 9, N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
+    else
+      k_dslash_m_epi_cap<P, NL6, N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
+  } else {
+    if (P == 64 || L.nl == 9)
+      k_dslash_m_epi<P, 9, N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
+    else
+      k_dslash_m_epi<P, NL6, N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
+  }
   return last_launch_status();
 }
 
@@ -466,7 +482,11 @@ static int batch_solve_p(const stag_batch_item* items, int nitems, const stag_so
     }
     bool steady = true;  // every live group begins with its direction update
     for (int k : live) steady = steady && groups[k]->pending_p;
-    if (!steady) {
+    // one group on one stream: its kernels are long enough that the host
+    // stays ahead of the GPU, so the chunk is queued directly (and the
+    // library's per-launch profiler can time it); graphs pay off when
+    // several groups run side by side
+    if (!steady || ng == 1) {
       // first chunk after a start or a reliable update: queue directly
       for (int k : live) TRYB(groups[k]->iterations(C));
       for (int k : live) TRYB(cuda_status(cudaStreamSynchronize(groups[k]->st)));

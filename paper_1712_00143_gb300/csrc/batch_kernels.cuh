@@ -9,9 +9,8 @@
 namespace stag {
 
 constexpr int MB = 128;  // threads per block of the N-RHS kernels
-
 template <int P, int NL, int N>
-__global__ void __launch_bounds__(MB) k_dslash_m(DslashArgsM<P> a, SpinorM<P> out, const int* flags) {
+__device__ __forceinline__ void dslash_m_body(const DslashArgsM<P>& a, SpinorM<P> out, const int* flags) {
   if (stopped(flags)) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.g.Vh) return;
@@ -21,12 +20,29 @@ __global__ void __launch_bounds__(MB) k_dslash_m(DslashArgsM<P> a, SpinorM<P> ou
   for (int r = 0; r < N; ++r) SpinorLoadM<P>::st(out, s, r, d[r]);
 }
 
+template <int P, int NL, int N>
+__global__ void __launch_bounds__(MB) k_dslash_m(DslashArgsM<P> a, SpinorM<P> out, const int* flags) {
+  dslash_m_body<P, NL, N>(a, out, flags);
+}
+
+// FP32 with up to four right-hand sides fits in 80 registers without
+// spilling: six resident blocks (24 warps) hide more latency than the five
+// an uncapped build allows.  (The FP64 and 16-bit kernels would spill.)
+constexpr int MRHS_CAPPED_MINB = 6;
+__host__ __device__ constexpr bool mrhs_capped(int p, int n) { return p == 32 && n <= 4; }
+
+template <int P, int NL, int N>
+__global__ void __launch_bounds__(MB, MRHS_CAPPED_MINB) k_dslash_m_cap(DslashArgsM<P> a, SpinorM<P> out,
+                                                                      const int* flags) {
+  dslash_m_body<P, NL, N>(a, out, flags);
+}
+
 // out_r = ax x_r + ay y_r + ad (D in)_r; RED = 1: Re<x_r, out_r>, RED = 2:
 // ||out_r||^2, one FP64 sum per system, finalised by the last block.
 template <int P, int NL, int N, int RED>
-__global__ void __launch_bounds__(MB)
-    k_dslash_m_epi(DslashArgsM<P> a, SpinorM<Acc<P>::value> out, SpinorM<P> x, double ax,
-                   SpinorM<Acc<P>::value> y, double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags) {
+__device__ __forceinline__ void dslash_m_epi_body(const DslashArgsM<P>& a, SpinorM<Acc<P>::value> out, SpinorM<P> x,
+                                                  double ax, SpinorM<Acc<P>::value> y, double ay, double ad,
+                                                  RedBuf rb, RedTarget tgt, const int* flags) {
   using A2 = typename Prec<P>::A2;
   using A = typename Prec<P>::A;
   constexpr int PA = Acc<P>::value;
@@ -70,6 +86,20 @@ __global__ void __launch_bounds__(MB)
     }
   }
   if (RED) grid_reduce<N>(red, rb, tgt);
+}
+
+template <int P, int NL, int N, int RED>
+__global__ void __launch_bounds__(MB)
+    k_dslash_m_epi(DslashArgsM<P> a, SpinorM<Acc<P>::value> out, SpinorM<P> x, double ax, SpinorM<Acc<P>::value> y,
+                   double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags) {
+  dslash_m_epi_body<P, NL, N, RED>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
+}
+
+template <int P, int NL, int N, int RED>
+__global__ void __launch_bounds__(MB, MRHS_CAPPED_MINB)
+    k_dslash_m_epi_cap(DslashArgsM<P> a, SpinorM<Acc<P>::value> out, SpinorM<P> x, double ax,
+                       SpinorM<Acc<P>::value> y, double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags) {
+  dslash_m_epi_body<P, NL, N, RED>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
 }
 
 // ------------------------------------------------------------ level 1

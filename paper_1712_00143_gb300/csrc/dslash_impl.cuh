@@ -326,7 +326,7 @@ int launch_dslash(const stag_lattice_s* lat, Spinor<P> out, Spinor<P> in, int ou
                   cudaStream_t st) {
   const LinkCopy& L = lat->links[prec_index<P>()];
   if (!L.present) return STAG_EINVAL;
-  ProfScope ps("dslash", st);
+  ProfScope ps(P == 64 ? "dslash64" : "dslash", st);
   return plain_with_shape<P>(lat, L.shape_plain, out, in, out_parity, flags, st);
 }
 
@@ -336,7 +336,7 @@ int launch_dslash_epi(const stag_lattice_s* lat, Spinor<Acc<P>::value> out, Spin
                       RedScratch rs, RedTarget tgt, const int* flags, cudaStream_t st) {
   const LinkCopy& L = lat->links[prec_index<P>()];
   if (!L.present) return STAG_EINVAL;
-  ProfScope ps("dslash_epi", st);
+  ProfScope ps(P == 64 ? "dslash64_epi" : "dslash_epi", st);
   return epi_with_shape<P>(lat, L.shape_epi, out, in, out_parity, x, ax, y, ay, ad, red, rs, tgt, flags, st);
 }
 
