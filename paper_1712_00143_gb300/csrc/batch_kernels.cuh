@@ -52,6 +52,9 @@ __device__ __forceinline__ void dslash_m_epi_body(const DslashArgsM<P>& a, Spino
 #pragma unroll
   for (int r = 0; r < N; ++r) red[r] = 0.0;
   if (s < a.g.Vh) {
+    // the epilogue's x_r are read after the stencil: start them towards L2 now
+#pragma unroll
+    for (int r = 0; r < N; ++r) prefetch_spinor_l2<P>(SpinorLoadM<P>::one(x, r), s);
     A2 d[N][3];
     dslash_site_m<P, NL, N>(a, s, d);
     const A cx = (A)ax, cd = (A)ad, cy = (A)ay;

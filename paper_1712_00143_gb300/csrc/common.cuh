@@ -250,6 +250,20 @@ template <> struct SpinorLoad<32> {
   }
 };
 
+// L2 prefetch of one site's vector (no registers): issued at the start of a
+// kernel whose epilogue reads the vector only after a long computation.
+template <int P> __device__ __forceinline__ void prefetch_spinor_l2(const Spinor<P>& f, int s) {
+  if constexpr (P == 32) {
+    const float2* p = (const float2*)f.v;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + c * (size_t)f.Vh + s));
+  } else if constexpr (P == 64) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"((const double2*)f.v + 3 * (size_t)s));
+  } else {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"((const uint4*)f.v + s));
+  }
+}
+
 // 16-bit records.  FP16: components stored as value/max (round to nearest
 // even), scale = max.  Fixed point: components stored as round(value/max *
 // 32767), scale = max/32767.  max = largest |re|, |im| of the site.
@@ -660,6 +674,9 @@ template <int NV> __device__ __forceinline__ void grid_reduce(double (&v)[NV], R
   double w[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) w[i] = 0.0;
+  // unrolled so that the loads of several partials are in flight together;
+  // each thread still adds its partials in block order (deterministic)
+#pragma unroll 8
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
 #pragma unroll
     for (int i = 0; i < NV; ++i) w[i] += __ldcg(rb.partials + i * gridDim.x + b);

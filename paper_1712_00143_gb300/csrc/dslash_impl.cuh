@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(B, MINB)
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   double red[1] = {0.0};
   if (s < a.g.Vh) {
+    prefetch_spinor_l2<P>(x, s);  // read by the epilogue, after the stencil
     A2 d[3], xv[3], o[3];
     dslash_site<P, NL>(a, s, d);
     SpinorLoad<P>::ld(x, s, xv);
