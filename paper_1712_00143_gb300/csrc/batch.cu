@@ -307,8 +307,17 @@ template <int P, int N> struct Group : GroupBase {
         TRYB(last_launch_status());
       }
       TRYB((mdslash<P, N>(lat, t, p, 1, flags, st)));
-      TRYB((mdslash_epi<P, N, 1>(lat, Ap, t, 0, p, shift, none, 0.0, -1.0, rs, RedTarget{RED_MCG_ALPHA, dst, nullptr},
+      // Ap = shift p - D_eo t without a reduction in the operator kernel, then
+      // <p, Ap> per system in a pass of its own: measured faster than the
+      // fused form, whose per-block reductions hold every block of the
+      // operator grid (4096 at 32^4) until its slowest warp is done
+      TRYB((mdslash_epi<P, N, 0>(lat, Ap, t, 0, p, shift, none, 0.0, -1.0, rs, RedTarget{RED_STORE, nullptr, nullptr},
                                  flags, st)));
+      {
+        ProfScope ps("reduce", st);
+        k_mcg_pap<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(p, Ap, dst, RedBuf{rs.partials, rs.counter});
+      }
+      TRYB(last_launch_status());
       {
         ProfScope ps("blas", st);
         k_mcg_update<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(xh, rh, p, Ap, dst,

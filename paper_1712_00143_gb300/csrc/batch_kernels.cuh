@@ -150,6 +150,35 @@ __global__ void __launch_bounds__(256) k_mcg_update(SpinorM<Acc<P>::value> xh, S
   grid_reduce<N>(red, rb, RedTarget{RED_MCG_BETA, g, nullptr});
 }
 
+// Re<p_r, Ap_r> -> alpha_r (RED_MCG_ALPHA): the CG dot product read back
+// from the operator's stored output, in a level-1 pass of its own (see the
+// group's iteration for why it is not fused into the operator kernel).
+template <int P, int N>
+__global__ void __launch_bounds__(256) k_mcg_pap(SpinorM<P> p, SpinorM<Acc<P>::value> Ap, McgState* g, RedBuf rb) {
+  constexpr int PV = Acc<P>::value;
+  using A = typename Prec<PV>::A;
+  if (stopped(&g->flags)) return;
+  Acc1<A> acc[N];
+  MGRID(s, p.Vh) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      typename Prec<P>::A2 pv[3];
+      typename Prec<PV>::A2 ap[3];
+      SpinorLoadM<P>::ld(p, s, r, pv);
+      SpinorLoadM<PV>::ld(Ap, s, r, ap);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[r].add_prod((A)pv[c].x, ap[c].x);
+        acc[r].add_prod((A)pv[c].y, ap[c].y);
+      }
+    }
+  }
+  double red[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) red[r] = acc[r].value();
+  grid_reduce<N>(red, rb, RedTarget{RED_MCG_ALPHA, g, nullptr});
+}
+
 // p_r = rh_r + beta_r p_r
 template <int P, int N>
 __global__ void __launch_bounds__(256) k_mcg_xpay(SpinorM<P> p, SpinorM<Acc<P>::value> rh, McgState* g) {
