@@ -111,3 +111,27 @@ def test_batch_full_workload_12_lattices():
             k += 1
         h.free()
     print(f"batched 96 systems on 12 lattices: {el:.3f} s")
+
+
+def test_batch_headline_workload_32_4_four_sources():
+    """The bench's chosen form exactly: 32^4, m = 0.01, the four seeded
+    Gaussian sources in one stag_batch_solve call (mixed32, one group of
+    four), every solution judged by the oracle's FP64 operator on sampled
+    sites and by the library's FP64 true residual."""
+    stag = _stag()
+    dims, mass = (32, 32, 32, 32), 0.01
+    fat, lng = synth.gauge_field(dims, 0.3, 1000)
+    h = stag.stag_load_links(dims, dev(fat), dev(lng), recon_long=12)
+    b = np.stack([synth.gaussian_source(dims, 5000 + k) for k in range(4)])
+    bd = dev(b)
+    x = torch.zeros_like(bd)
+    infos = stag.stag_batch_solve([(h, x, bd, 4, mass)], mode="mixed32", tol=1e-10)
+    xh = x.cpu().numpy()
+    rng = np.random.default_rng(8)
+    sites = np.unique(rng.integers(0, b.shape[1], 500))
+    for i in range(4):
+        assert infos[i]["converged"] and infos[i]["true_rel_resid"] <= 1e-10, (i, infos[i])
+        mx = oracle.apply_m_at_sites(fat, lng, xh[i], mass, dims, sites)
+        r = b[i][sites] - mx
+        assert np.linalg.norm(r) / np.linalg.norm(b[i][sites]) < 3e-10
+    h.free()
