@@ -148,6 +148,10 @@ __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t
   asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
 
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
 __device__ int g_tc_error;  // set (never cleared by kernels) when a bounded wait gave up
 
 constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds at GB300 clocks
@@ -228,6 +232,9 @@ __global__ void __launch_bounds__(128, 4)
       }
       src = act_ptr(hin, 16, Vh, np, ns) + half * 24;
     }
+    // packed bf16 words of this thread's 8 channels for the six rows: [row][word]
+    // (words 0, 1 from channel group g = 0, words 2, 3 from g = 1), hi and lo
+    uint32_t hw[6][4], lw[6][4];
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
       float2 t[4][3];
@@ -267,13 +274,18 @@ __global__ void __launch_bounds__(128, 4)
         float x[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) x[c] = (j & 1) ? t[c][i].y : t[c][i].x;
-        uint32_t h0, l0, h1, l1;
-        split2(x[0], x[1], h0, l0);
-        split2(x[2], x[3], h1, l1);
-        const uint32_t off = (uint32_t)op_offset(j * TILE + s_local, half * 8 + g * 4);
-        st_shared_v2(hi_base + off, h0, h1);
-        st_shared_v2(lo_base + off, l0, l1);
+        split2(x[0], x[1], hw[j][2 * g], lw[j][2 * g]);
+        split2(x[2], x[3], hw[j][2 * g + 1], lw[j][2 * g + 1]);
       }
+    }
+    // one 16-byte store per row and part: a quarter-warp's eight lanes (eight
+    // consecutive rows of one core matrix) cover 128 contiguous bytes, free of
+    // bank conflicts (two 8-byte stores per row collided four ways)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const uint32_t off = (uint32_t)op_offset(j * TILE + s_local, half * 8);
+      st_shared_v4(hi_base + off, hw[j][0], hw[j][1], hw[j][2], hw[j][3]);
+      st_shared_v4(lo_base + off, lw[j][0], lw[j][1], lw[j][2], lw[j][3]);
     }
     fence_async_smem();
     __syncthreads();
