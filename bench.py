@@ -675,7 +675,9 @@ def run_config(args):
         per_site = (time.perf_counter() - t0) / lat.V
         print(json.dumps({"config": "link construction (3-staple fat + Naik) from thin links, FP64",
                           "unit": "s", "results": rows,
+                          "algorithm": "three-link staples stored once, reused by every loop",
                           "roofline": {"bound": "fp64_alu", "flop_per_link": flop_per_link,
+                                       "flop_per_link_walking_each_staple": flop_walk,
                                        "note": "FP64 peak about 1.2 TFLOP/s on GB300 (measured DGEMM 1.10)"},
                           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "16^4, scaled per site",
                                            "s_per_site": per_site,
@@ -689,9 +691,14 @@ def run_config(args):
 
         beta = 6.0
         coef = ogf.luscher_weisz_coefficients(0.87)
-        # per link: 6 plaquette staples x 2 products + 42 five-link staples x 4
-        # products (216 flop each), 48 coefficient updates (36 flop), U Sigma and TA
-        flop_per_link = (6 * 2 + 42 * 4 + 1) * 216 + 48 * 36 + 60
+        # executed flop per link of the staple-reuse algorithm: the staple table
+        # (24 staples per site x 2 complex 3x3 products of 216 flop, a quarter per
+        # link) and, per (nu, s), rectangles 1-2 (4 products), rectangle 3 and the
+        # four parallelograms (5 products + the shared left factor), coefficient
+        # updates; then U Sigma and TA.  Walking every staple link by link instead
+        # (MILC's baseline, Sec. 4.2) costs 40884 flop per link.
+        flop_per_link = 24 * 2 * 216 // 4 + 6 * (10 * 216 + 7 * 36 + 18) + 216 + 40
+        flop_walk = (6 * 2 + 42 * 4 + 1) * 216 + 48 * 36 + 60
         rows = {}
         for dims in ((24, 24, 24, 24), (32, 32, 32, 32)):
             lat = Lattice(dims)
@@ -701,14 +708,15 @@ def run_config(args):
             stag.stag_profile_reset()
             stag.stag_profile_select("gauge_force", 1)
             stag.stag_profile_enable(True)
-            wall, _ = _timed(lambda: stag.stag_gauge_force(dims, thin, beta, *coef, force=F), reps=3)
-            n, ms = stag.stag_profile_read("gauge_force")
+            reps = 3
+            wall, _ = _timed(lambda: stag.stag_gauge_force(dims, thin, beta, *coef, force=F), reps=reps)
+            n, ms = stag.stag_profile_read("gauge_force")  # two kernels per call
             stag.stag_profile_enable(False)
             stag.stag_profile_select("", 1)
-            per = ms / max(n, 1) * 1e-3
-            rows["x".join(map(str, dims))] = {"device_s": per, "wall_s": wall,
+            per = ms / reps * 1e-3
+            rows["x".join(map(str, dims))] = {"device_s": per, "wall_s": wall, "launches_per_call": n / reps,
                                               "fp64_tflops": 4 * lat.V * flop_per_link / per / 1e12,
-                                              "gflops_per_site": 4 * flop_per_link / 1e9}
+                                              "gflop_per_site": 4 * flop_per_link / 1e9}
             del thin, F
             torch.cuda.empty_cache()
         # the oracle on a 4^4 x 6 sample (numpy, one core), scaled per link
@@ -721,7 +729,9 @@ def run_config(args):
         print(json.dumps({"config": "Symanzik one-loop gauge force (plaquette, rectangle, parallelogram), FP64",
                           "coefficients": {"beta": beta, "u0": 0.87, "c_pl": coef[0], "c_rt": coef[1], "c_pg": coef[2]},
                           "unit": "s", "results": rows,
+                          "algorithm": "three-link staples stored once, reused by every loop",
                           "roofline": {"bound": "fp64_alu", "flop_per_link": flop_per_link,
+                                       "flop_per_link_walking_each_staple": flop_walk,
                                        "note": "FP64 peak about 1.2 TFLOP/s on GB300 (measured DGEMM 1.10)"},
                           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "4^4 x 6, scaled per link",
                                            "s_per_link": per_link, "value_24_4": per_link * 4 * 24 ** 4}}),
