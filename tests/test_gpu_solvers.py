@@ -139,3 +139,32 @@ def test_zero_source_and_non_unitary_links():
     with pytest.raises(stag.StagError) as e:
         stag.stag_load_links(dims, f.fat_d, f.fat_d, recon_long=12)
     assert e.value.status == stag.STAG_ENOTUNITARY
+
+
+def test_empty_and_invalid_inputs_are_rejected():
+    """Empty inputs (no items, no right-hand sides, no shifts) and invalid
+    values are refused with STAG_EINVAL before any work, and the handle
+    stays usable afterwards."""
+    stag = _stag()
+    dims, mass = (8, 8, 8, 8), 0.1
+    f = Field.get(dims)
+    h = f.handle(recon=12)
+    b = dev(synth.gaussian_source(dims, 9300))
+    x = torch.zeros_like(b)
+    empty = torch.zeros((0, h.Vh, 3), dtype=torch.complex128, device="cuda")
+    cases = [
+        lambda: stag.stag_batch_solve([], mode="mixed32"),
+        lambda: stag.stag_batch_solve([(h, empty, empty, 0, mass)], mode="mixed32"),
+        lambda: stag.stag_multishift_cg(h, [], b, mass, []),
+        lambda: stag.stag_dslash(h, empty, empty, 1, "fp32", nrhs=0),
+        lambda: stag.stag_cg(h, x, b, mass, mode="mixed32", tol=0.0),
+        lambda: stag.stag_cg(h, x, b, mass, mode="mixed32", delta=1.5),
+        lambda: stag.stag_dslash(h, x, b, 2, "fp32"),
+    ]
+    for k, case in enumerate(cases):
+        with pytest.raises(stag.StagError) as err:
+            case()
+        assert err.value.status == stag.STAG_EINVAL, (k, err.value)
+    info = stag.stag_cg(h, x, b, mass, mode="mixed32", tol=1e-10)
+    assert info["converged"]
+    h.free()
