@@ -168,3 +168,27 @@ def test_empty_and_invalid_inputs_are_rejected():
     info = stag.stag_cg(h, x, b, mass, mode="mixed32", tol=1e-10)
     assert info["converged"]
     h.free()
+
+
+def test_solves_are_bit_reproducible():
+    """Fixed-order reductions: the same solve twice gives bit-identical
+    solutions and iteration counts (single-system and batched)."""
+    stag = _stag()
+    dims, mass = (8, 8, 8, 8), 0.05
+    f = Field.get(dims)
+    h = f.handle(recon=12)
+    b = dev(synth.gaussian_source(dims, 9400))
+    outs = []
+    for _ in range(2):
+        x = torch.zeros_like(b)
+        info = stag.stag_cg(h, x, b, mass, mode="mixedfx16", tol=1e-10)
+        outs.append((x.clone(), info["iters"]))
+    assert outs[0][1] == outs[1][1] and torch.equal(outs[0][0], outs[1][0])
+    B = dev(np.stack([synth.gaussian_source(dims, 9410 + k) for k in range(3)]))
+    res = []
+    for _ in range(2):
+        X = torch.zeros_like(B)
+        infos = stag.stag_batch_solve([(h, X, B, 3, mass)], mode="mixed32", tol=1e-10)
+        res.append((X.clone(), [i["iters"] for i in infos]))
+    assert res[0][1] == res[1][1] and torch.equal(res[0][0], res[1][0])
+    h.free()
