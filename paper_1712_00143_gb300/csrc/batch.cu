@@ -196,6 +196,7 @@ struct GroupBase {
   virtual int start(const stag_solve_params& prm) = 0;
   virtual int iterations(int C) = 0;
   virtual int reliable_update() = 0;
+  virtual int round_dev(int C) = 0;
   virtual int finish() = 0;
 };
 
@@ -225,10 +226,10 @@ template <int P, int N> struct Group : GroupBase {
     return get_red_scratch(lat, (pre + "red").c_str(), &rs, 2 * N);
   }
 
-  // FP64: r = b - shift y + D_eo D_oe y, ||r_i||^2 -> tgt
-  int true_residual(RedTarget tgt) {
-    TRYB((mdslash<64, N>(lat, t64, y64, 1, nullptr, st)));
-    return mdslash_epi<64, N, 2>(lat, r64, t64, 0, y64, -shift, b64, 1.0, 1.0, rs, tgt, nullptr, st);
+  // FP64: r = b - shift y + D_eo D_oe y, ||r_i||^2 -> tgt (stop: a stop word, or nullptr)
+  int true_residual(RedTarget tgt, const int* stop = nullptr) {
+    TRYB((mdslash<64, N>(lat, t64, y64, 1, stop, st)));
+    return mdslash_epi<64, N, 2>(lat, r64, t64, 0, y64, -shift, b64, 1.0, 1.0, rs, tgt, stop, st);
   }
 
   int setup(const stag_solve_params& prm) override {
@@ -277,6 +278,10 @@ template <int P, int N> struct Group : GroupBase {
     }
     h.active = active;
     if (active == 0 || prm.max_iter <= 0) h.flags = F_CONVERGED;
+    h.done = active == 0 ? 1 : 0;
+    h.status = STAG_OK;
+    h.ru_skip = F_CONVERGED;
+    h.skip_xpay = 1;
     *hst = h;
     TRYB(cuda_status(cudaMemcpyAsync(dst, hst, sizeof(McgState), cudaMemcpyHostToDevice, st)));
     const int G = grid_bw(lat->g.Vh);
@@ -303,7 +308,7 @@ template <int P, int N> struct Group : GroupBase {
     for (int i = 0; i < C; ++i) {
       if (pending_p) {
         ProfScope ps("blas", st);
-        k_mcg_xpay<P, N><<<grid_bw(Vh), 256, 0, st>>>(p, rh, dst);
+        k_mcg_xpay<P, N><<<grid_bw(Vh), 256, 0, st>>>(p, rh, dst, nullptr);
         TRYB(last_launch_status());
       }
       TRYB((mdslash<P, N>(lat, t, p, 1, flags, st)));
@@ -329,26 +334,71 @@ template <int P, int N> struct Group : GroupBase {
     return STAG_OK;
   }
 
-  int reliable_update() override {
+  int reliable_update() override { return ru_kernels(nullptr); }
+
+  // the update's kernels; with stop = &dst->ru_skip they run only when a
+  // reliable update is due (graph-resident loop)
+  int ru_kernels(const int* stop) {
     const int Vh = lat->g.Vh;
     {
       ProfScope ps("blas", st);
-      k_maccumulate<PV, N><<<grid_bw(Vh), 256, 0, st>>>(y64, xh);
+      k_maccumulate<PV, N><<<grid_bw(Vh), 256, 0, st>>>(y64, xh, stop);
     }
     TRYB(last_launch_status());
-    TRYB(true_residual(RedTarget{RED_MCG_RU_RESID, dst, nullptr}));
+    TRYB(true_residual(RedTarget{RED_MCG_RU_RESID, dst, nullptr}, stop));
     {
       ProfScope ps("reduce", st);
       k_mru_convert_dot<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(rh, r64, p, dst,
-                                                                          RedBuf{rs.partials, rs.counter});
+                                                                          RedBuf{rs.partials, rs.counter}, stop);
     }
     TRYB(last_launch_status());
     {
       ProfScope ps("blas", st);
-      k_mru_p<P, N><<<grid_bw(Vh), 256, 0, st>>>(p, rh, dst);
+      k_mru_p<P, N><<<grid_bw(Vh), 256, 0, st>>>(p, rh, dst, stop);
     }
     TRYB(last_launch_status());
     pending_p = false;
+    return STAG_OK;
+  }
+
+  // One round of the graph-resident loop for this group: a reliable update
+  // if one is due (gate, the update's kernels, decide), then C iterations
+  // whose first direction update is skipped after a start or an update.
+  int round_dev(int C) override {
+    const int* flags = &dst->flags;
+    const int Vh = lat->g.Vh;
+    SpinorM<PV> none{nullptr, Vh, N};
+    count_launch();
+    k_mcg_ru_gate<<<1, 1, 0, st>>>(dst);
+    TRYB(last_launch_status());
+    TRYB(ru_kernels(&dst->ru_skip));
+    count_launch();
+    k_mcg_ru_decide<<<1, 1, 0, st>>>(dst);
+    TRYB(last_launch_status());
+    for (int i = 0; i < C; ++i) {
+      {
+        ProfScope ps("blas", st);
+        k_mcg_xpay<P, N><<<grid_bw(Vh), 256, 0, st>>>(p, rh, dst, &dst->skip_xpay);
+      }
+      TRYB(last_launch_status());
+      count_launch();
+      k_mcg_clear_skip<<<1, 1, 0, st>>>(dst);
+      TRYB(last_launch_status());
+      TRYB((mdslash<P, N>(lat, t, p, 1, flags, st)));
+      TRYB((mdslash_epi<P, N, 0>(lat, Ap, t, 0, p, shift, none, 0.0, -1.0, rs, RedTarget{RED_STORE, nullptr, nullptr},
+                                 flags, st)));
+      {
+        ProfScope ps("reduce", st);
+        k_mcg_pap<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(p, Ap, dst, RedBuf{rs.partials, rs.counter});
+      }
+      TRYB(last_launch_status());
+      {
+        ProfScope ps("blas", st);
+        k_mcg_update<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(xh, rh, p, Ap, dst,
+                                                                        RedBuf{rs.partials, rs.counter});
+      }
+      TRYB(last_launch_status());
+    }
     return STAG_OK;
   }
 
@@ -403,6 +453,83 @@ struct GraphExec {
 };
 double now_b() { return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count(); }
 }  // namespace
+
+// The graph-resident loop over all groups (see batch_solve_p).
+static int dev_loop(std::vector<std::unique_ptr<GroupBase>>& groups, cudaStream_t cap, Streams& streams, int C,
+                    int budget) {
+  const int ng = (int)groups.size();
+  McgState** gs_dev = nullptr;
+  int* budget_dev = nullptr;
+  if (cudaMalloc(&gs_dev, sizeof(McgState*) * ng) != cudaSuccess || cudaMalloc(&budget_dev, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    if (gs_dev) cudaFree(gs_dev);
+    return STAG_ENOMEM;
+  }
+  struct Free {
+    void* a;
+    void* b;
+    ~Free() {
+      cudaFree(a);
+      cudaFree(b);
+    }
+  } freer{gs_dev, budget_dev};
+  std::vector<McgState*> gs(ng);
+  for (int k = 0; k < ng; ++k) gs[k] = groups[k]->dst;
+  TRYB(cuda_status(cudaMemcpyAsync(gs_dev, gs.data(), sizeof(McgState*) * ng, cudaMemcpyHostToDevice, cap)));
+  TRYB(cuda_status(cudaMemcpyAsync(budget_dev, &budget, sizeof(int), cudaMemcpyHostToDevice, cap)));
+  TRYB(cuda_status(cudaStreamSynchronize(cap)));
+
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  struct GFree {
+    cudaGraph_t* g;
+    cudaGraphExec_t* e;
+    ~GFree() {
+      if (*e) cudaGraphExecDestroy(*e);
+      if (*g) cudaGraphDestroy(*g);
+    }
+  } gfree{&graph, &exec};
+  TRYB(cuda_status(cudaGraphCreate(&graph, 0)));
+  cudaGraphConditionalHandle handle;
+  TRYB(cuda_status(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault)));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = handle;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  TRYB(cuda_status(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np)));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+
+  set_capturing(true);
+  int s = cuda_status(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  if (!s) s = cuda_status(cudaEventRecord(streams.ev[1], cap));
+  for (int k = 0; k < ng && !s; ++k) s = cuda_status(cudaStreamWaitEvent(groups[k]->st, streams.ev[1], 0));
+  for (int k = 0; k < ng && !s; ++k) s = groups[k]->round_dev(C);
+  for (int k = 0; k < ng && !s; ++k) {
+    s = cuda_status(cudaEventRecord(streams.ev[2 + k], groups[k]->st));
+    if (!s) s = cuda_status(cudaStreamWaitEvent(cap, streams.ev[2 + k], 0));
+  }
+  if (!s) {
+    count_launch();
+    k_mcg_loop_cond<<<1, 1, 0, cap>>>(gs_dev, ng, budget_dev, handle);
+    s = last_launch_status();
+  }
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cap, &out);
+  const long long per_round = set_capturing(false);
+  if (s || e != cudaSuccess) {
+    cudaGetLastError();
+    return s ? s : STAG_ECUDA;
+  }
+  TRYB(cuda_status(cudaGraphInstantiate(&exec, graph, 0)));
+  TRYB(cuda_status(cudaGraphLaunch(exec, cap)));
+  TRYB(cuda_status(cudaStreamSynchronize(cap)));
+  int left = 0;
+  TRYB(cuda_status(cudaMemcpy(&left, budget_dev, sizeof(int), cudaMemcpyDeviceToHost)));
+  for (long long i = 0; i < per_round * (long long)(budget - left); ++i) count_launch();
+  return STAG_OK;
+}
 
 template <int P>
 static int batch_solve_p(const stag_batch_item* items, int nitems, const stag_solve_params& prm,
@@ -480,7 +607,23 @@ static int batch_solve_p(const stag_batch_item* items, int nitems, const stag_so
   }
   streams.s.push_back(cap);
   long long chunks = 0, max_chunks = (long long)prm.max_iter / C + 64 * ng + 64;
-  for (;;) {
+  if (ng > 1) {
+    // Several groups: the whole solve is one graph launch.  A WHILE node's
+    // body runs one round for every group side by side (its reliable update
+    // if due, then C iterations) and a last kernel sets the loop condition:
+    // another round while any group is live, at most max_chunks rounds.
+    TRYB(dev_loop(groups, cap, streams, C, (int)std::min<long long>(max_chunks, 1 << 30)));
+    for (auto& g : groups) {
+      TRYB(cuda_status(cudaMemcpyAsync(g->hst, g->dst, sizeof(McgState), cudaMemcpyDeviceToHost, cap)));
+    }
+    TRYB(cuda_status(cudaStreamSynchronize(cap)));
+    for (auto& g : groups) {
+      g->done = true;
+      if (g->hst->done == 0) g->status = STAG_ENOTCONV;  // the round budget ran out
+      else g->status = g->hst->status;
+    }
+  }
+  for (; ng == 1;) {
     std::vector<int> live;
     for (int k = 0; k < ng; ++k)
       if (!groups[k]->done) live.push_back(k);

@@ -181,10 +181,11 @@ __global__ void __launch_bounds__(256) k_mcg_pap(SpinorM<P> p, SpinorM<Acc<P>::v
 
 // p_r = rh_r + beta_r p_r
 template <int P, int N>
-__global__ void __launch_bounds__(256) k_mcg_xpay(SpinorM<P> p, SpinorM<Acc<P>::value> rh, McgState* g) {
+__global__ void __launch_bounds__(256) k_mcg_xpay(SpinorM<P> p, SpinorM<Acc<P>::value> rh, McgState* g,
+                                                   const int* skip) {
   using A2 = typename Prec<P>::A2;
   using A = typename Prec<P>::A;
-  if (stopped(&g->flags)) return;
+  if (stopped(&g->flags) || (skip && __ldcg(skip))) return;
   A beta[N];
 #pragma unroll
   for (int r = 0; r < N; ++r) beta[r] = (A)__ldcg(&g->sys[r].beta);
@@ -206,7 +207,8 @@ __global__ void __launch_bounds__(256) k_mcg_xpay(SpinorM<P> p, SpinorM<Acc<P>::
 }
 
 // y_r += xh_r; xh_r = 0
-template <int PV, int N> __global__ void k_maccumulate(SpinorM<64> y, SpinorM<PV> xh) {
+template <int PV, int N> __global__ void k_maccumulate(SpinorM<64> y, SpinorM<PV> xh, const int* stop) {
+  if (stopped(stop)) return;
   MGRID(s, y.Vh) {
 #pragma unroll
     for (int r = 0; r < N; ++r) {
@@ -229,10 +231,12 @@ template <int PV, int N> __global__ void k_maccumulate(SpinorM<64> y, SpinorM<PV
 
 // rh_r = r64_r (rounded); <rh_r, p_r> -> RED_MCG_RU_ORTHO (2N values)
 template <int P, int N>
-__global__ void k_mru_convert_dot(SpinorM<Acc<P>::value> rh, SpinorM<64> r64, SpinorM<P> p, McgState* g, RedBuf rb) {
+__global__ void k_mru_convert_dot(SpinorM<Acc<P>::value> rh, SpinorM<64> r64, SpinorM<P> p, McgState* g, RedBuf rb,
+                                  const int* stop) {
   constexpr int PV = Acc<P>::value;
   using A2 = typename Prec<PV>::A2;
   using A = typename Prec<PV>::A;
+  if (stopped(stop)) return;  // every block alike: no partial reduction is left behind
   Acc1<A> re[N], im[N];
   MGRID(s, r64.Vh) {
 #pragma unroll
@@ -268,9 +272,11 @@ __global__ void k_mru_convert_dot(SpinorM<Acc<P>::value> rh, SpinorM<64> r64, Sp
 }
 
 // p_r = rh_r + beta_r (p_r - c_r rh_r)
-template <int P, int N> __global__ void k_mru_p(SpinorM<P> p, SpinorM<Acc<P>::value> rh, McgState* g) {
+template <int P, int N>
+__global__ void k_mru_p(SpinorM<P> p, SpinorM<Acc<P>::value> rh, McgState* g, const int* stop) {
   using A2 = typename Prec<P>::A2;
   using A = typename Prec<P>::A;
+  if (stopped(stop)) return;
   A beta[N], cr[N], ci[N];
 #pragma unroll
   for (int r = 0; r < N; ++r) {
@@ -371,5 +377,55 @@ template <int P, int N> __global__ void k_mnorm2(SpinorM<P> v, RedBuf rb, RedTar
 }
 
 #undef MGRID
+
+// ------------------------------------------------------------ graph-resident loop control
+// Before a group's reliable-update kernels in each round of the loop: is an
+// update due (a flag set by the last chunk)?  ru_skip = 0 lets the update's
+// kernels run, F_CONVERGED makes them return at once.
+__global__ void k_mcg_ru_gate(McgState* g) {
+  if (g->done) {
+    g->ru_skip = F_CONVERGED;
+    return;
+  }
+  if (g->flags & F_BREAKDOWN) {
+    g->done = 1;
+    g->status = STAG_EBREAKDOWN;
+    g->ru_skip = F_CONVERGED;
+    return;
+  }
+  g->ru_skip = (g->flags & (F_CONVERGED | F_NEED_RU | F_ITER_CAP)) ? 0 : F_CONVERGED;
+}
+
+// After them: retire the group (every system at its target, an error, the
+// iteration cap) or let it iterate on from the new direction.
+__global__ void k_mcg_ru_decide(McgState* g) {
+  if (g->ru_skip) return;
+  g->ru_skip = F_CONVERGED;
+  if (g->flags & F_BREAKDOWN) {
+    g->done = 1;
+    g->status = STAG_EBREAKDOWN;
+  } else if (g->active == 0) {
+    g->done = 1;
+    g->flags |= F_CONVERGED;
+  } else if (g->iter >= g->max_iter) {
+    g->done = 1;
+    g->status = STAG_ENOTCONV;
+    g->flags |= F_ITER_CAP;
+  } else {
+    g->skip_xpay = 1;  // the update formed the direction already
+  }
+}
+
+__global__ void k_mcg_clear_skip(McgState* g) { g->skip_xpay = 0; }
+
+// End of a round: another one while any group is live and the budget of
+// rounds lasts (the budget bounds the loop whatever the solver state).
+__global__ void k_mcg_loop_cond(McgState* const* gs, int ng, int* budget, cudaGraphConditionalHandle h) {
+  int live = 0;
+  for (int k = 0; k < ng; ++k) live |= !__ldcg(&gs[k]->done);
+  const int b = *budget - 1;
+  *budget = b;
+  cudaGraphSetConditional(h, (live && b > 0) ? 1u : 0u);
+}
 
 }  // namespace stag

@@ -372,6 +372,11 @@ struct McgState {
   int iter, max_iter;
   int reliable_updates;
   CgState sys[MAX_RHS];
+  // control of the graph-resident solve loop (several groups)
+  int done;       // 1: the group needs no more work (converged, or ended by an error)
+  int status;     // STAG_OK or the error that ended the group
+  int ru_skip;    // F_CONVERGED while no reliable update is due (a stop word for its kernels), else 0
+  int skip_xpay;  // 1: the next direction update must not run (after the start or an update)
 };
 
 enum RedOp : int {
