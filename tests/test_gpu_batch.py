@@ -135,3 +135,34 @@ def test_batch_headline_workload_32_4_four_sources():
         r = b[i][sites] - mx
         assert np.linalg.norm(r) / np.linalg.norm(b[i][sites]) < 3e-10
     h.free()
+
+
+def test_batch_several_groups_iteration_cap():
+    """Several groups (the graph-resident loop) with max_iter far below what
+    convergence needs: every system ends with ENOTCONV after its reliable
+    update at the cap, the call returns (the loop terminates), and x holds
+    the last iterate, whose true residual is the one reported."""
+    stag = _stag()
+    specs = [((8, 8, 8, 8), 0.01, 3, 1003), ((4, 6, 8, 10), 0.01, 2, 1004)]
+    items, keep = [], []
+    for dims, mass, nrhs, seed in specs:
+        fat, lng = synth.gauge_field(dims, 0.3, seed)
+        h = stag.stag_load_links(dims, dev(fat), dev(lng), recon_long=12)
+        b = synth.gaussian_source(dims, 6000 + seed, nrhs=nrhs)
+        bd = dev(b)
+        x = torch.zeros_like(bd)
+        items.append((h, x, bd, nrhs, mass))
+        keep.append((dims, fat, lng, mass, b, x, h))
+    infos = stag.stag_batch_solve(items, mode="mixed32", tol=1e-10, max_iter=30, raise_on_error=False)
+    assert infos[0]["return"] == stag.STAG_ENOTCONV
+    k = 0
+    for dims, fat, lng, mass, b, x, h in keep:
+        xh = x.cpu().numpy()
+        for i in range(b.shape[0]):
+            assert infos[k]["status"] == stag.STAG_ENOTCONV and not infos[k]["converged"], infos[k]
+            assert 30 <= infos[k]["iters"] <= 30 + 16, infos[k]
+            # x is the last iterate: the reported true residual is the oracle's for it
+            res = oracle.true_residual(fat, lng, xh[i], b[i], mass, dims)
+            assert np.isfinite(res) and abs(infos[k]["true_rel_resid"] - res) < 1e-9 * max(1.0, res), (infos[k], res)
+            k += 1
+        h.free()
