@@ -675,9 +675,7 @@ def run_config(args):
         per_site = (time.perf_counter() - t0) / lat.V
         print(json.dumps({"config": "link construction (3-staple fat + Naik) from thin links, FP64",
                           "unit": "s", "results": rows,
-                          "algorithm": "three-link staples stored once, reused by every loop",
                           "roofline": {"bound": "fp64_alu", "flop_per_link": flop_per_link,
-                                       "flop_per_link_walking_each_staple": flop_walk,
                                        "note": "FP64 peak about 1.2 TFLOP/s on GB300 (measured DGEMM 1.10)"},
                           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "16^4, scaled per site",
                                            "s_per_site": per_site,
