@@ -531,7 +531,8 @@ def run_config(args):
     stag_cg per system; `learned` training and evaluating the network
     preconditioner on 32^4; `netpass` one network forward and one
     loss-and-gradient pass on 32^4; `links` fat and Naik links built from
-    thin links on the GPU; `gaugeforce` the Symanzik one-loop gauge force."""
+    thin links on the GPU; `gaugeforce` the Symanzik one-loop gauge force;
+    `fermionforce` the fermion force through the link construction."""
     import torch
 
     import paper_1712_00143_gb300 as stag
@@ -734,6 +735,59 @@ def run_config(args):
                           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "4^4 x 6, scaled per link",
                                            "s_per_link": per_link, "value_24_4": per_link * 4 * 24 ** 4}}),
               flush=True)
+    elif args.config == "fermionforce":
+        # fermion force of an 8-term rational pseudofermion action (FP64) on 24^4
+        # and 32^4: outer products of the 8 solution pairs, then the chain rule
+        # through the fat and Naik links
+        import numpy as np
+
+        import oracle.fermion_force as off
+
+        from synth.gauge import Lattice, thin_links
+
+        nt = 8
+        alphas = tuple(np.linspace(0.05, 0.4, nt))
+        # executed flop per link: the chain pass, 36 products of 3x3 complex
+        # matrices (216 flop each), 15 scalings (18 flop), TA (40); the outer
+        # pass, two 3x3 outer products accumulated per term (144 flop)
+        flop_per_link = 36 * 216 + 15 * 18 + 40 + 144 * nt
+        rows = {}
+        for dims in ((24, 24, 24, 24), (32, 32, 32, 32)):
+            lat = Lattice(dims)
+            thin = thin_links(lat, EPS, GAUGE_SEED).reshape(lat.V, 4, 3, 3).to(dev)
+            xs = torch.from_numpy(np.stack([synth.random_spinor(dims, 10 + i) for i in range(nt)])).to(dev)
+            ys = torch.from_numpy(np.stack([synth.random_spinor(dims, 50 + i) for i in range(nt)])).to(dev)
+            F = stag.stag_fermion_force(dims, thin, xs, ys, alphas)
+            torch.cuda.synchronize()
+            stag.stag_profile_reset()
+            stag.stag_profile_select("fermion_force", 1)
+            stag.stag_profile_enable(True)
+            reps = 3
+            wall, _ = _timed(lambda: stag.stag_fermion_force(dims, thin, xs, ys, alphas, force=F), reps=reps)
+            n, ms = stag.stag_profile_read("fermion_force")  # two kernels per call
+            stag.stag_profile_enable(False)
+            stag.stag_profile_select("", 1)
+            per = ms / reps * 1e-3
+            rows["x".join(map(str, dims))] = {"device_s": per, "wall_s": wall, "launches_per_call": n / reps,
+                                              "fp64_tflops": 4 * lat.V * flop_per_link / per / 1e12}
+            del thin, xs, ys, F
+            torch.cuda.empty_cache()
+        # the oracle on a 6^4 sample (numpy, one core), scaled per link
+        d = (6, 6, 6, 6)
+        lat = Lattice(d)
+        ts = thin_links(lat, EPS, GAUGE_SEED).reshape(lat.V, 4, 3, 3).numpy()
+        ox = [synth.random_spinor(d, 10 + i) for i in range(nt)]
+        oy = [synth.random_spinor(d, 50 + i) for i in range(nt)]
+        t0 = time.perf_counter()
+        off.fermion_force(ts, ox, oy, alphas, d)
+        per_link = (time.perf_counter() - t0) / (4 * lat.V)
+        print(json.dumps({"config": f"fermion force through the 3-staple fat + Naik links, {nt} terms, FP64",
+                          "unit": "s", "results": rows,
+                          "roofline": {"bound": "fp64_alu", "flop_per_link": flop_per_link,
+                                       "note": "FP64 peak about 1.2 TFLOP/s on GB300 (measured DGEMM 1.10)"},
+                          "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "6^4, scaled per link",
+                                           "s_per_link": per_link, "value_32_4": per_link * 4 * 32 ** 4}}),
+              flush=True)
     elif args.config == "learned":
         # 32^4, m = 0.01: 2000 (residual, error) pairs from the unpreconditioned
         # mixed CG on 24 training fields, network 1-16-16-16-1 trained on the
@@ -822,7 +876,7 @@ def main(argv=None):
     ap.add_argument("--net-dims", type=int, default=32, help="lattice extent of the netpass config")
     ap.add_argument("--config", default="headline",
                     choices=["headline", "small", "multishift", "batch", "learned", "netpass", "links",
-                             "gaugeforce"])
+                             "gaugeforce", "fermionforce"])
     ap.add_argument("--learned-pairs", type=int, default=2000)
     ap.add_argument("--learned-fields", type=int, default=24)
     ap.add_argument("--learned-epochs", type=int, default=2)

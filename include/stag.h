@@ -315,6 +315,31 @@ int stag_build_links(const int dims[4], const void* thin, void* fat, void* lng, 
 int stag_gauge_force(const int dims[4], const void* thin, void* force, double beta, double c_pl, double c_rt,
                      double c_pg, void* stream);
 
+/* Fermion force of the pseudofermion action of a rational approximation,
+ *   S = sum_i alpha_i phi^dag (M + sigma_i)^{-1} phi,   M = m^2 - D_eo D_oe,
+ * taken through the link construction of stag_build_links (fat link
+ * c1 U + c_staple (staples), Naik link c3 U U U): the paper's third benchmark
+ * routine, the HISQ fermion force (Sec. 4.2; the paper gives no formula).
+ * With X_i = (M + sigma_i)^{-1} phi on even sites and Y_i = D_oe X_i on odd
+ * sites (the caller solves, e.g. with stag_multishift_cg, and applies
+ * stag_dslash), the output is
+ *   force[y][nu] = -TA[U_nu(y) Z_nu(y)],  TA(A) = (A - A^dag)/2 - Tr(A - A^dag)/6,
+ * with dS = sum Re Tr[dU_nu(y) Z_nu(y)], so that U_nu(y) -> exp(eps X)
+ * U_nu(y) changes S by -eps Re Tr(X force) (the convention of
+ * stag_gauge_force).  FP64.
+ *   thin    : device, canonical [V][4][3][3] complex double, caller-owned.
+ *   x_even  : device, [n_terms][V/2][3] complex double, X_i (checkerboard
+ *             index lex / 2, the layout of every field of this API).
+ *   y_odd   : device, [n_terms][V/2][3] complex double, Y_i.
+ *   alpha   : host, n_terms weights; 1 <= n_terms <= 32.
+ *   force   : device, canonical [V][4][3][3] complex double, caller-owned,
+ *             not overlapping thin, x_even or y_odd (STAG_EINVAL).
+ * dims: even extents >= 4.  Scratch: 2 V x 4 x 9 complex doubles
+ * (1152 B per site), stream-ordered (STAG_ENOMEM if unavailable).
+ * Asynchronous on `stream`; profiler family "fermion_force". */
+int stag_fermion_force(const int dims[4], const void* thin, int n_terms, const void* x_even, const void* y_odd,
+                       const double* alpha, double c1, double c_staple, double c3, void* force, void* stream);
+
 /* Check of this build's tensor-core path on the current GPU (the path the
  * network's 16 -> 16 layers take): one tile of tcgen05 bfloat16 products
  * with FP32 accumulation in tensor memory, 9 accumulated steps, compared
@@ -335,7 +360,7 @@ const char* stag_strerror(int status);
  * plain and with the fused axpy/reduction epilogue), "dslash64",
  * "dslash64_epi" (FP64), "dslash_mrhs", "dslash_mrhs_epi", "dslash_mrhs64",
  * "dslash_mrhs64_epi" (multi-right-hand-side forms), "blas", "reduce",
- * "convert", "links", "net", "net_bwd", "gauge_force".  stag_launch_count
+ * "convert", "links", "net", "net_bwd", "gauge_force", "fermion_force".  stag_launch_count
  * counts all library kernel launches since the last reset, whether or not
  * profiling is on. */
 int stag_profile_enable(int on);

@@ -26,6 +26,15 @@ Parity status of each function (what pins it, checked by the CPU tests):
                               closed form, single-link insertion at the sites
                               the definition names, gauge covariance
                               (tests/test_links_oracle.py).
+  * gauge_force (module)   -- Symanzik one-loop gauge force: finite
+                              differences of the action per loop type, unit
+                              links, gauge covariance
+                              (tests/test_gauge_force_oracle.py).
+  * fermion_force (module) -- fermion force of a multi-shift pseudofermion
+                              action through the fat and Naik links: finite
+                              differences of the action (solved with cg) per
+                              term type, gauge covariance, planted errors
+                              caught (tests/test_fermion_force_oracle.py).
 """
 
 from .staggered import (

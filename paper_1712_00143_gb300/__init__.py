@@ -66,6 +66,7 @@ EXPORTS = (
     "stag_tc_selftest",
     "stag_build_links",
     "stag_gauge_force",
+    "stag_fermion_force",
     "stag_strerror",
     "stag_profile_enable",
     "stag_profile_select",
@@ -184,6 +185,7 @@ def load_library(path=LIB_PATH):
         "stag_tc_selftest": (ci, [ctypes.POINTER(cd)]),
         "stag_build_links": (ci, [ctypes.POINTER(ci), vp, vp, vp, cd, cd, cd, vp]),
         "stag_gauge_force": (ci, [ctypes.POINTER(ci), vp, vp, cd, cd, cd, cd, vp]),
+        "stag_fermion_force": (ci, [ctypes.POINTER(ci), vp, ci, vp, vp, ctypes.POINTER(cd), cd, cd, cd, vp, vp]),
         "stag_strerror": (ctypes.c_char_p, [ci]),
         "stag_profile_enable": (ci, [ci]),
         "stag_profile_select": (ci, [ctypes.c_char_p, ci]),
@@ -511,6 +513,24 @@ def stag_gauge_force(dims, thin, beta, c_pl, c_rt, c_pg, force=None, stream=None
     d = (ctypes.c_int * 4)(*[int(v) for v in dims])
     _check(_lib.stag_gauge_force(d, _ptr(thin, "thin", n), _ptr(force, "force", n), float(beta), float(c_pl),
                                  float(c_rt), float(c_pg), _stream(stream)), "stag_gauge_force")
+    return force
+
+
+def stag_fermion_force(dims, thin, xs, ys, alphas, c1=1.0, c_staple=0.125, c3=-1.0 / 24.0, force=None, stream=None):
+    """Fermion force (FP64) through the fat and Naik link construction.  thin:
+    canonical [V][4][3][3] complex128 CUDA tensor; xs: even-site solutions X_i
+    and ys: odd-site Y_i = D_oe X_i, contiguous [n][V/2][3] complex128 CUDA
+    tensors; alphas: n weights.  Returns the force, canonical [V][4][3][3]."""
+    V = int(dims[0]) * int(dims[1]) * int(dims[2]) * int(dims[3])
+    n = V * 36
+    nt = len(alphas)
+    force = torch.empty_like(thin) if force is None else force
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    a = (ctypes.c_double * max(nt, 1))(*[float(v) for v in alphas])
+    nf = nt * (V // 2) * 3
+    _check(_lib.stag_fermion_force(d, _ptr(thin, "thin", n), nt, _ptr(xs, "xs", nf), _ptr(ys, "ys", nf), a,
+                                   float(c1), float(c_staple), float(c3), _ptr(force, "force", n), _stream(stream)),
+           "stag_fermion_force")
     return force
 
 

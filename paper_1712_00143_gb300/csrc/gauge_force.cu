@@ -26,25 +26,6 @@ namespace stag {
 namespace gf {
 using namespace su3;
 
-struct Pos {
-  long long lex;
-  C4 c;
-};
-
-__device__ __forceinline__ Pos step(const Dims& d, Pos p, int dir, int k) {
-  Pos q;
-  q.lex = shifted(d, p.lex, p.c, dir, k);
-  const int L = extent(d, dir);
-  int w = p.c.get(dir) + k;
-  w = w >= L ? w - L : (w < 0 ? w + L : w);
-  q.c = p.c;
-  q.c.x = dir == 0 ? w : q.c.x;
-  q.c.y = dir == 1 ? w : q.c.y;
-  q.c.z = dir == 2 ? w : q.c.z;
-  q.c.t = dir == 3 ? w : q.c.t;
-  return q;
-}
-
 __device__ __forceinline__ M3 dagger(const M3& a) {
   M3 r;
 #pragma unroll

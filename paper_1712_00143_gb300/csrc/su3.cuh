@@ -1,6 +1,6 @@
 // su3.cuh -- FP64 3x3 complex matrix products and periodic site stepping on
-// the canonical lex layout, shared by the link construction and the gauge
-// force kernels.
+// the canonical lex layout, shared by the link construction, the gauge force
+// and the fermion force kernels.
 #pragma once
 #include "internal.h"
 
@@ -79,6 +79,51 @@ __device__ __forceinline__ void mac_mul(M3& acc, const M3& a, const M3& b) {
       for (int k = 0; k < 3; ++k) cmac(acc.e[3 * i + j], a.e[3 * i + k], b.e[3 * k + j]);
 }
 
+// acc += a^dag b
+__device__ __forceinline__ void mac_dag_mul(M3& acc, const M3& a, const M3& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        // conj(a_ki) b_kj
+        const double2 x = a.e[3 * k + i], y = b.e[3 * k + j];
+        acc.e[3 * i + j].x = fma(x.x, y.x, fma(x.y, y.y, acc.e[3 * i + j].x));
+        acc.e[3 * i + j].y = fma(x.x, y.y, fma(-x.y, y.x, acc.e[3 * i + j].y));
+      }
+}
+
+// acc += a^dag b^dag = acc + (b a)^dag
+__device__ __forceinline__ void mac_dag_mul_dag(M3& acc, const M3& a, const M3& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        // conj(a_ki) conj(b_jk) = conj(a_ki b_jk)
+        const double2 x = a.e[3 * k + i], y = b.e[3 * j + k];
+        acc.e[3 * i + j].x = fma(x.x, y.x, fma(-x.y, y.y, acc.e[3 * i + j].x));
+        acc.e[3 * i + j].y = fma(-x.x, y.y, fma(-x.y, y.x, acc.e[3 * i + j].y));
+      }
+}
+
+__device__ __forceinline__ M3 zero3() {
+  M3 r;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) r.e[i] = make_double2(0.0, 0.0);
+  return r;
+}
+
+__device__ __forceinline__ void scale3(M3& a, double c) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    a.e[i].x *= c;
+    a.e[i].y *= c;
+  }
+}
+
 struct Dims {
   int L0, L1, L2, L3;
 };
@@ -103,6 +148,39 @@ __device__ __forceinline__ long long shifted(const Dims& d, long long x, const C
   int w = v + k;
   w = w >= L ? w - L : (w < 0 ? w + L : w);
   return x + stride(d, mu) * (long long)(w - v);
+}
+
+// A site as its lex index and coordinates, moved along one direction at a time.
+struct Pos {
+  long long lex;
+  C4 c;
+};
+
+__device__ __forceinline__ Pos pos_of(const Dims& d, long long x) {
+  Pos p;
+  p.lex = x;
+  long long r = x;
+  p.c.x = (int)(r % d.L0);
+  r /= d.L0;
+  p.c.y = (int)(r % d.L1);
+  r /= d.L1;
+  p.c.z = (int)(r % d.L2);
+  p.c.t = (int)(r / d.L2);
+  return p;
+}
+
+__device__ __forceinline__ Pos step(const Dims& d, Pos p, int dir, int k) {
+  Pos q;
+  q.lex = shifted(d, p.lex, p.c, dir, k);
+  const int L = extent(d, dir);
+  int w = p.c.get(dir) + k;
+  w = w >= L ? w - L : (w < 0 ? w + L : w);
+  q.c = p.c;
+  q.c.x = dir == 0 ? w : q.c.x;
+  q.c.y = dir == 1 ? w : q.c.y;
+  q.c.z = dir == 2 ? w : q.c.z;
+  q.c.t = dir == 3 ? w : q.c.t;
+  return q;
 }
 
 }  // namespace su3
