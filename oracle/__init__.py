@@ -11,7 +11,11 @@ Parity status of each function (what pins it, checked by the CPU tests):
                               anti-hermiticity D_eo = -D_oe^dag, gauge
                               covariance under random SU(3) transforms, full
                               free-field spectrum of a dense 4^4 build.
-  * cg                     -- dense LU solve (numpy.linalg.solve) on 4^4.
+  * cg                     -- dense LU solve (numpy.linalg.solve) on 4^4;
+                              its Lanczos Ritz values / kappa estimate
+                              (lanczos_ritz_values) by the exact spectrum of
+                              a diagonal matrix after n steps and by the
+                              dense 4^4 spectrum (numpy.linalg.eigvalsh).
   * multishift_cg          -- dense LU solve per shift on 4^4, and single-mass
                               CG run shift by shift.
   * true_residual          -- exact definition ||b - M x|| / ||b||.

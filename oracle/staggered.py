@@ -146,7 +146,12 @@ def cg(fat, lng, b, mass, dims, tol=1e-10, max_iter=100000, x0=None, shift=0.0):
     Iterates until the recursively updated residual satisfies
     ||r|| <= tol ||b||, then recomputes r = b - A x; if that true residual
     still exceeds the target, CG continues from (x, r_true).
-    Returns (x, info) with info = {iters, true_rel_resid, converged}.
+    Returns (x, info) with info = {iters, true_rel_resid, converged,
+    ritz, kappa_est}: the eigenvalues of the Lanczos tridiagonal that CG's
+    alpha and beta define (up to the first true-residual restart, after
+    which the recurrence is no longer a Lanczos one), and the ratio of the
+    largest to the smallest, an estimate of the condition number of
+    (M + shift) from below.
     """
     A = lambda v: apply_m(fat, lng, v, mass, dims, shift)  # noqa: E731
     x = np.zeros_like(b) if x0 is None else x0.astype(np.complex128, copy=True)
@@ -157,6 +162,7 @@ def cg(fat, lng, b, mass, dims, tol=1e-10, max_iter=100000, x0=None, shift=0.0):
     target = tol * tol * bb
     it = 0
     converged = rr <= target
+    alphas, betas, lanczos = [], [], True
     while not converged and it < max_iter:
         Ap = A(p)
         pAp = _dot(p, Ap).real
@@ -165,15 +171,44 @@ def cg(fat, lng, b, mass, dims, tol=1e-10, max_iter=100000, x0=None, shift=0.0):
         r -= alpha * Ap
         rr_new = _dot(r, r).real
         it += 1
+        if lanczos:
+            alphas.append(alpha)
         if rr_new <= target:
             r = b - A(x)
             rr_new = _dot(r, r).real
             converged = rr_new <= target
+            lanczos = False
         beta = rr_new / rr
+        if lanczos:
+            betas.append(beta)
         p = r + beta * p
         rr = rr_new
     res = true_residual(fat, lng, x, b, mass, dims, shift)
-    return x, {"iters": it, "true_rel_resid": res, "converged": res <= tol}
+    ritz = lanczos_ritz_values(alphas, betas)
+    info = {"iters": it, "true_rel_resid": res, "converged": res <= tol, "ritz": ritz,
+            "kappa_est": float(ritz[-1] / ritz[0]) if len(ritz) else float("nan")}
+    return x, info
+
+
+def lanczos_ritz_values(alphas, betas):
+    """Eigenvalues (ascending) of the Lanczos tridiagonal T_k of k CG steps.
+
+    CG's coefficients define it (Golub and Van Loan, Sec. 10.2; Saad,
+    Iterative Methods, Sec. 6.7.3): with alpha_j the step lengths and
+    beta_j = |r_{j+1}|^2 / |r_j|^2,
+        T_jj     = 1/alpha_j + beta_{j-1}/alpha_{j-1}   (second term absent for j = 0)
+        T_j,j+1  = sqrt(beta_j) / alpha_j.
+    Only the betas of steps followed by another step enter the off-diagonal.
+    """
+    k = len(alphas)
+    if k == 0:
+        return np.zeros(0)
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < k:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(betas[j]) / alphas[j]
+    return np.linalg.eigvalsh(T)
 
 
 def multishift_cg(fat, lng, b, mass, shifts, dims, tol=1e-10, max_iter=100000):

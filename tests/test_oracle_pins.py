@@ -329,3 +329,64 @@ def test_planted_dropped_naik_backward_fails_free_field(monkeypatch):
     monkeypatch.setattr(ost, "dslash", patched)
     assert free_field_error((4, 6, 8, 10), C1_ASQTAD, C3_ASQTAD, 0.1, MOMENTA_ASYM) > 1e-3
     assert calls["n"] > 0
+
+
+# ------------------------------------------------- Lanczos estimate of kappa
+
+
+def _cg_coefficients(A, b, steps):
+    """alpha_j and beta_j of plain CG on a small dense SPD matrix (test-side)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = r @ r
+    al, be = [], []
+    for _ in range(steps):
+        Ap = A @ p
+        a = rr / (p @ Ap)
+        x += a * p
+        r -= a * Ap
+        rr_new = r @ r
+        al.append(a)
+        be.append(rr_new / rr)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return al, be
+
+
+def test_lanczos_ritz_values_recover_a_diagonal_spectrum():
+    """n CG steps on an n x n matrix with distinct eigenvalues: the Lanczos
+    tridiagonal is similar to the matrix, so its eigenvalues are exactly the
+    matrix's (Golub and Van Loan, Sec. 10.2)."""
+    d = np.array([0.5, 1.0, 2.5, 4.0, 7.0, 11.0])
+    al, be = _cg_coefficients(np.diag(d), np.ones(6), 6)
+    np.testing.assert_allclose(oracle.staggered.lanczos_ritz_values(al, be), d, rtol=1e-10)
+
+
+def test_cg_ritz_values_bracket_the_dense_spectrum(dense_4444):
+    """The oracle CG's Ritz values lie inside [lambda_min, lambda_max] of the
+    dense 4^4 operator, and the extremes converge to them: kappa_est is the
+    condition number that numpy.linalg.eigvalsh gives."""
+    dims, fat, lng, mass, M, b = dense_4444
+    lam = np.linalg.eigvalsh(M)
+    _, info = oracle.cg(fat, lng, b, mass, dims, tol=1e-12)
+    r = info["ritz"]
+    assert lam[0] * (1 - 1e-12) <= r[0] and r[-1] <= lam[-1] * (1 + 1e-12)
+    assert abs(r[-1] - lam[-1]) < 1e-12 * lam[-1]
+    assert abs(r[0] - lam[0]) < 1e-6 * lam[0]
+    assert abs(info["kappa_est"] - lam[-1] / lam[0]) < 1e-6 * lam[-1] / lam[0]
+
+
+def test_planted_lanczos_error_fails_closed_form(monkeypatch):
+    def broken(alphas, betas):  # off-diagonal without the square root
+        k = len(alphas)
+        T = np.zeros((k, k))
+        for j in range(k):
+            T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+            if j + 1 < k:
+                T[j, j + 1] = T[j + 1, j] = betas[j] / alphas[j]
+        return np.linalg.eigvalsh(T)
+
+    monkeypatch.setattr(oracle.staggered, "lanczos_ritz_values", broken)
+    with pytest.raises(AssertionError):
+        test_lanczos_ritz_values_recover_a_diagonal_spectrum()
