@@ -61,6 +61,23 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert L.stag_cg(None, one, one, 0.1, None, None, None) == stag.STAG_EINVAL
     assert L.stag_multishift_cg(None, None, one, 0.1, None, 0, None, None, None) == stag.STAG_EINVAL
     assert L.stag_free_lattice(None) == stag.STAG_EINVAL
+    # the FP64 routines around the solver refuse bad arguments before any CUDA call
+    two = ctypes.c_void_p(1 << 40)
+    three = ctypes.c_void_p(1 << 41)
+    alpha = (ctypes.c_double * 33)(*([1.0] * 33))
+    assert L.stag_build_links(dims, None, one, two, 1.0, 0.125, -1 / 24, None) == stag.STAG_EINVAL
+    assert L.stag_build_links(odd, one, two, three, 1.0, 0.125, -1 / 24, None) == stag.STAG_EINVAL
+    assert L.stag_build_links(dims, one, one, two, 1.0, 0.125, -1 / 24, None) == stag.STAG_EINVAL  # fat == thin
+    assert L.stag_gauge_force(dims, None, one, 6.0, 1.0, 0.0, 0.0, None) == stag.STAG_EINVAL
+    assert L.stag_gauge_force(small, one, two, 6.0, 1.0, 0.0, 0.0, None) == stag.STAG_EINVAL
+    assert L.stag_gauge_force(dims, one, one, 6.0, 1.0, 0.0, 0.0, None) == stag.STAG_EINVAL  # force == thin
+    ff = L.stag_fermion_force
+    assert ff(dims, one, 0, two, three, alpha, 1.0, 0.125, -1 / 24, ctypes.c_void_p(1 << 42), None) == stag.STAG_EINVAL
+    assert ff(dims, one, 33, two, three, alpha, 1.0, 0.125, -1 / 24, ctypes.c_void_p(1 << 42), None) == stag.STAG_EINVAL
+    assert ff(dims, one, 1, two, three, None, 1.0, 0.125, -1 / 24, ctypes.c_void_p(1 << 42), None) == stag.STAG_EINVAL
+    assert ff(odd, one, 1, two, three, alpha, 1.0, 0.125, -1 / 24, ctypes.c_void_p(1 << 42), None) == stag.STAG_EINVAL
+    assert ff(dims, one, 1, two, three, alpha, 1.0, 0.125, -1 / 24, one, None) == stag.STAG_EINVAL  # force == thin
+    assert ff(dims, one, 1, two, three, alpha, 1.0, 0.125, -1 / 24, two, None) == stag.STAG_EINVAL  # force == x
     assert stag.strerror(stag.STAG_ENOTCONV).startswith("solver did not converge")
 
 
