@@ -124,6 +124,9 @@ void stag_default_params(stag_solve_params* p);
 int stag_load_links(stag_lattice_t* out, const int dims[4], const void* fat, const void* lng,
                     const stag_link_opts* opts, void* stream);
 
+/* Release a handle from stag_load_links: waits for all device work
+ * (cudaDeviceSynchronize), then frees every device buffer the handle owns.
+ * The handle must not be used afterwards.  NULL: EINVAL. */
 int stag_free_lattice(stag_lattice_t lat);
 
 /* The launch shape the autotuner kept for a copy's Dslash kernel
@@ -266,7 +269,14 @@ enum stag_loss { STAG_LOSS_ERROR = 0, STAG_LOSS_RESIDUAL = 1 };
  * identity (self direction maps channel c to c with weight 1, gates open),
  * so an untrained network makes flexible CG behave like CG. */
 int stag_net_create(stag_net_t* out, const int* channels, int nlayers, unsigned long long seed);
+/* Release a network: waits for all device work, then frees its weights,
+ * optimiser moments and gradient buffers.  NULL: EINVAL. */
 int stag_net_free(stag_net_t net);
+/* Number of parameters in the flat host layout of get/set params: for each
+ * layer l, W[9][C_out][C_in] (direction 0 = the site itself; 1 + 2 mu and
+ * 2 + 2 mu = the forward and backward fat-link hops of direction mu)
+ * followed, except after the last layer, by the gate biases b[C_out].
+ * -1 for a NULL handle. */
 long long stag_net_num_params(stag_net_t net);
 /* host copies of the parameters; rounded = 1 returns the weights as the
  * kernels use them (bfloat16 values), 0 the FP32 master copy */
@@ -369,8 +379,13 @@ int stag_profile_enable(int on);
  * `every` of each family (every <= 1: all), which keeps the events' own cost
  * out of the measured workload. */
 int stag_profile_select(const char* families, int every);
+/* Zero every family's launch count and time, and the launch counter. */
 int stag_profile_reset(void);
+/* Launches and summed device time (ms) of one family since the last reset
+ * (waits for the pending events).  Unknown family: 0 launches; NULL family:
+ * EINVAL. */
 int stag_profile_read(const char* family, long long* launches, double* total_ms);
+/* All library kernel launches since the last reset. */
 long long stag_launch_count(void);
 
 #ifdef __cplusplus
