@@ -38,7 +38,8 @@ Gradients use the convention G = dL/dRe + i dL/dIm for complex fields, so a
 linear map y = A h has G_h = A^dag G_y.
 
 Parity status: forward, backward and both losses are pinned by finite
-differences of the loss in FP64 and by gauge covariance
+differences of the loss in FP64 and by gauge covariance; the restriction of
+the forward pass to sampled output sites is pinned by the whole-field forward
 (tests/test_network_oracle.py).
 """
 
@@ -128,6 +129,57 @@ def forward(fat, params, r, dims, parity_sites):
         cache["h"].append(h)
     pred = h[0, parity_sites]
     return pred / scale, cache
+
+
+def forward_at_sites(fat, params, r, dims, parity_sites, out_sites):
+    """The even-site output z = N(r) at checkerboard indices ``out_sites`` only.
+
+    The same definition as :func:`forward`, restricted to what those outputs
+    read: a layer's output at x depends on its input at x and x +- mu, so with
+    L layers left the input is needed on the sites within L hops of the
+    requested ones.  The site sets S_L (the requested sites) and S_{k-1} =
+    S_k and its neighbours are built first; layer k is evaluated on S_{k+1}
+    from its input on S_k.  The input scale sqrt(Vh)/||r|| is the global one.
+    Returns a [len(out_sites)][3] array in the order of ``out_sites``.
+    """
+    dims = tuple(dims)
+    nl = len(params)
+    Vh = len(parity_sites)
+    scale = np.sqrt(Vh) / np.linalg.norm(r)
+    targets = np.asarray(parity_sites)[np.asarray(out_sites, dtype=np.int64)]
+    sets = [None] * (nl + 1)
+    sets[nl] = np.unique(targets)
+    for k in range(nl, 0, -1):
+        c = staggered.site_coords(dims, sets[k])
+        nb = [sets[k]] + [staggered.neighbour_lex(dims, c, mu, s) for mu in range(4) for s in (1, -1)]
+        sets[k - 1] = np.unique(np.concatenate(nb))
+    lex0 = sets[0]
+    c0 = staggered.site_coords(dims, lex0)
+    even = c0.sum(axis=1) % 2 == 0
+    h = np.zeros((1, len(lex0), 3), dtype=np.complex128)
+    h[0, even] = r[lex0[even] // 2] * scale
+    for k, (W, b) in enumerate(params):
+        X, Y = sets[k + 1], sets[k]
+        cX = staggered.site_coords(dims, X)
+        pre = np.zeros((W.shape[1], len(X), 3), dtype=np.complex128)
+        for d in range(NDIR):
+            pre += np.einsum("ab,bvi->avi", W[d], _transport_on(fat, h, Y, X, cX, dims, d))
+        h = gate(pre, b)[0] if b is not None else pre
+    return h[0, np.searchsorted(sets[nl], targets)] / scale
+
+
+def _transport_on(fat, h, Y, X, cX, dims, d):
+    """(T_d h) on the sorted lex sites X, for h given on the sorted lex sites Y
+    (Y holds X and its +-mu neighbours)."""
+    if d == 0:
+        return h[:, np.searchsorted(Y, X)]
+    mu = (d - 1) // 2
+    eta = staggered.staggered_phase(mu, cX)[None, :, None]
+    if d % 2 == 1:  # +1/2 eta F_mu(x) h(x + mu)
+        nb = staggered.neighbour_lex(dims, cX, mu, +1)
+        return 0.5 * eta * np.einsum("vij,cvj->cvi", fat[X, mu], h[:, np.searchsorted(Y, nb)])
+    nb = staggered.neighbour_lex(dims, cX, mu, -1)  # -1/2 eta F_mu(x - mu)^dag h(x - mu)
+    return -0.5 * eta * np.einsum("vji,cvj->cvi", np.conj(fat[nb, mu]), h[:, np.searchsorted(Y, nb)])
 
 
 def loss(fat, params, r, e, dims, parity_sites):

@@ -198,3 +198,22 @@ def test_residual_loss_equals_m_weighted_error(setup, with_long):
     zhat = cache["h"][-1][0, even]
     want = np.linalg.norm(oracle.apply_m(fat, lng, zhat - e * s, MASS, DIMS)) ** 2 / np.linalg.norm(r * s) ** 2
     assert abs(L - want) < 1e-11 * max(1.0, want)
+
+
+@pytest.mark.parametrize("dims", [(8, 6, 8, 10), (4, 4, 4, 6)])
+def test_forward_at_sites_equals_the_whole_field_forward(dims):
+    """The sampled-site forward (layer k evaluated only on the sites within
+    L - k hops of the requested outputs) must reproduce the whole-field
+    forward at those sites: on 8x6x8x10 the four-hop neighbourhoods stay
+    well inside the lattice, on 4^3x6 they wrap around it."""
+    fat, _ = synth.gauge_field(dims, 0.3, 1040)
+    even = oracle.parity_sites(dims, 0)
+    r = synth.random_spinor(dims, 23)
+    params = net.init_params((1, 3, 2, 2, 1), seed=4)
+    rng = np.random.default_rng(2)
+    params = [(W, None if b is None else rng.normal(0.0, 0.5, b.shape)) for W, b in params]
+    z, _ = net.forward(fat, params, r, dims, even)
+    sites = np.concatenate([rng.integers(0, len(even), 12), [0, len(even) - 1, 5]])
+    zs = net.forward_at_sites(fat, params, r, dims, even, sites)
+    assert zs.shape == (len(sites), 3)
+    assert np.abs(zs - z[sites]).max() < 1e-13 * np.abs(z).max()
