@@ -47,12 +47,17 @@ FLOP_PER_SITE = 1146
 # algorithmic bytes per output site of one Dslash: 16 link matrices (8 fat x
 # 9 complex + 8 Naik x NL complex) read once, the input vector read once,
 # the output written once
-ELEM_BYTES = {"fp64": 16, "fp32": 8, "fp16": 4, "fx16": 4}
-VEC_BYTES = {"fp64": 48, "fp32": 24, "fp16": 16, "fx16": 16}
+ELEM_BYTES = {"fp64": 16, "fp32": 8, "fp16": 4, "fx16": 4, "df64": 16}
+VEC_BYTES = {"fp64": 48, "fp32": 24, "fp16": 16, "fx16": 16, "df64": 48}
 MODE_PREC = {"plain64": "fp64", "mixed32": "fp32", "mixed16": "fp16", "mixedfx16": "fx16"}
 # arithmetic type of the Krylov loop of each solver mode (FP32 arithmetic on
 # 16-bit storage for the 16-bit modes)
 DTYPE = {"plain64": "f64", "mixed32": "f32", "mixed16": "f32", "mixedfx16": "f32"}
+
+
+# the library's kernel families (stag.h, instrumentation)
+FAMILIES = ("dslash", "dslash_epi", "dslash64", "dslash64_epi", "dslash_mrhs", "dslash_mrhs_epi", "dslash_mrhs64",
+            "dslash_mrhs64_epi", "dslash_df", "dslash_df_epi", "blas", "reduce", "convert")
 
 
 def dslash_bytes_per_site(prec, recon):
@@ -296,8 +301,18 @@ def run_gpu(args, rank, world, local_rank):
     shapes = {k: stag.stag_tuned_shape(h, MODE_PREC[CHOSEN], i) for i, k in enumerate(("plain", "epilogue"))}
     n_d, ms_d = stag.stag_profile_read(fam_plain)
     n_e, ms_e = stag.stag_profile_read(fam_epi)
-    stag.stag_profile_enable(False)
+    # one more (untimed) step with every launch of every family timed: where
+    # the device time of a step goes
+    stag.stag_profile_reset()
     stag.stag_profile_select("", 1)
+    step(CHOSEN)
+    torch.cuda.synchronize()
+    breakdown = {}
+    for fam in FAMILIES:
+        n, ms = stag.stag_profile_read(fam)
+        if n:
+            breakdown[fam] = {"launches": n, "ms": round(ms, 3)}
+    stag.stag_profile_enable(False)
     ms_total = reduce_max(e0.elapsed_time(e1), world)
     ms_per_step = ms_total / args.steps
     value = ms_per_step / 1e3 / NSRC
@@ -393,6 +408,8 @@ def run_gpu(args, rank, world, local_rank):
                 "algorithmic_bytes_per_launch": bytes_launch,
                 "launches_timed": n_d,
                 "launches_sampled_every": 8,
+                "launches_excluded": "chunks of queued iterations cut short by a stop flag (reliable-update "
+                "trigger, convergence): their launches after the flag return at once",
                 "avg_launch_us": per_launch_ms * 1e3,
                 "gflops": FLOP_PER_SITE * sites_launch / (per_launch_ms * 1e-3) / 1e9,
                 "epilogue_variant_avg_us": ms_e / max(n_e, 1) * 1e3,
@@ -407,12 +424,31 @@ def run_gpu(args, rank, world, local_rank):
                 "h2d_bytes_per_step": NSRC * vec_bytes,
                 "d2h_bytes_per_step": NSRC * vec_bytes,
             },
+            "step_breakdown_ms": breakdown,
+            "reliable_update_operator": df_summary(breakdown, Vh, NSRC),
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
     h.free()
     return result
+
+
+def df_summary(breakdown, Vh, nrhs):
+    """The reliable updates' FP64-class operator (double-float, links read
+    once for up to four right-hand sides): device time per launch and its
+    algorithmic bytes (links 2304 B per site, nrhs input and output vectors
+    of 48 B; the epilogue form also reads y and b)."""
+    out = {}
+    for fam, extra in (("dslash_df", 0), ("dslash_df_epi", 2)):
+        ent = breakdown.get(fam)
+        if not ent:
+            continue
+        us = ent["ms"] / ent["launches"] * 1e3
+        byt = (2304 + (2 + extra) * 48 * nrhs) * Vh
+        out[fam] = {"launches": ent["launches"], "avg_launch_us": us, "algorithmic_bytes_per_launch": byt,
+                    "GB/s": byt / (us * 1e-6) / 1e9, "arithmetic": "double-float on the FP32 pipes"}
+    return out or None
 
 
 # ------------------------------------------------------------------ reference arm (oracle)
@@ -477,7 +513,7 @@ def run_dslash_sweep(args):
         del fat, lng
         for recon in args.sweep_recons:
             for prec in args.sweep_precs:
-                if prec == "fp64" and recon == 12:
+                if prec in ("fp64", "df64") and recon == 12:
                     continue
                 h = stag.stag_load_links(dims, fd, ld, recon_long=recon, prec_mask=1 << stag.PREC[prec])
                 for nrhs in args.sweep_nrhs:
@@ -486,6 +522,8 @@ def run_dslash_sweep(args):
                         psi = psi.unsqueeze(0).repeat(nrhs, 1, 1).contiguous()
                     out = torch.empty_like(psi)
                     fam = ("dslash" if nrhs == 1 else "dslash_mrhs") + ("64" if prec == "fp64" else "")
+                    if prec == "df64":
+                        fam = "dslash_df"
                     for _ in range(3):
                         stag.stag_dslash(h, out, psi, 1, prec, nrhs=nrhs)
                     torch.cuda.synchronize()
@@ -497,15 +535,16 @@ def run_dslash_sweep(args):
                     n, ms = stag.stag_profile_read(fam)
                     stag.stag_profile_enable(False)
                     stag.stag_profile_select("", 1)
-                    per = ms / max(n, 1)  # one launch covers min(nrhs, 8) right-hand sides
-                    k = nrhs if nrhs <= 8 else 8
+                    per = ms / max(n, 1)  # one launch covers min(nrhs, 8) (double-float: 4) right-hand sides
+                    k = min(nrhs, 4 if prec == "df64" else 8)
                     nl = 6 if (recon == 12 and prec != "fp64") else 9
                     byt = ((8 * 9 + 8 * nl) * ELEM_BYTES[prec] + 2 * k * VEC_BYTES[prec]) * h.Vh
                     gbs = byt / (per * 1e-3) / 1e9
                     print(json.dumps({"dslash": "x".join(map(str, dims)), "prec": prec, "recon": recon, "nrhs": k,
                                       "us": per * 1e3, "GB/s": gbs, "frac": gbs / peak, "peak_kind": peak_kind,
                                       "GFLOP/s": FLOP_PER_SITE * k * h.Vh / (per * 1e-3) / 1e9,
-                                      "us_per_rhs": per * 1e3 / k, "bytes_per_launch": byt}), flush=True)
+                                      "us_per_rhs": per * 1e3 / k, "bytes_per_launch": byt,
+                                      "tuned_shape": stag.stag_tuned_shape(h, prec, 0)}), flush=True)
                     del psi, out
                 h.free()
         del fd, ld
@@ -559,7 +598,7 @@ def run_config(args):
         shifts = [10 ** (-4 + k / 2) for k in range(9)]
         fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
         h = stag.stag_load_links(dims, torch.from_numpy(fat).to(dev), torch.from_numpy(lng).to(dev), recon_long=12,
-                                 prec_mask=0b1011)
+                                 prec_mask=0b11011)
         del fat, lng
         b = torch.from_numpy(synth.gaussian_source(dims, 5000)).to(dev)
         xs = [torch.zeros_like(b) for _ in shifts]
@@ -579,7 +618,7 @@ def run_config(args):
         for j, dims in enumerate(dims_list):
             fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED + j)
             h = stag.stag_load_links(dims, torch.from_numpy(fat).to(dev), torch.from_numpy(lng).to(dev), recon_long=12,
-                                     prec_mask=0b1011)
+                                     prec_mask=0b11011)
             bd = torch.from_numpy(synth.gaussian_source(dims, 5000 + 100 * j, nrhs=8)).to(dev)
             items.append((h, torch.zeros_like(bd), bd, 8, masses[j % 3]))
         res = {}
@@ -804,7 +843,7 @@ def run_config(args):
         for j in range(ntrain):
             fat, lng = synth.gauge_field(dims, EPS, 1000 + j)
             h = stag.stag_load_links(dims, torch.from_numpy(fat).to(dev), torch.from_numpy(lng).to(dev), recon_long=12,
-                                     prec_mask=0b0011)
+                                     prec_mask=0b10011)
             del fat, lng
             handles.append(h)
             b = torch.from_numpy(synth.gaussian_source(dims, 5000 + 100 * j)).to(dev)

@@ -53,15 +53,26 @@ extern "C" {
 /* --------------------------------------------------------------- precision */
 /* STAG_FP16: IEEE binary16 storage.  STAG_FX16: 16-bit fixed point (15
  * fraction bits) in units of a per-site (vectors) or per-field (links) scale.
- * Both keep one FP32 scale per site for vectors and compute in FP32. */
-typedef enum { STAG_FP64 = 0, STAG_FP32 = 1, STAG_FP16 = 2, STAG_FX16 = 3 } stag_prec;
+ * Both keep one FP32 scale per site for vectors and compute in FP32.
+ * STAG_DF64: FP64-class "double-float": links and vectors carried as the sum
+ * hi + lo of two floats (about 48 significant bits; links split once at load,
+ * 16 bytes per complex like FP64), products and sums by error-free
+ * transformations on the FP32 pipes (GB300 runs FP64 arithmetic at a small
+ * fraction of its FP32 rate).  Relative error of the operator about 1e-14.
+ * The mixed-precision solvers compute their reliable updates (the true
+ * residual b - M y) in this format when the handle holds its link copy, and
+ * in FP64 otherwise. */
+typedef enum { STAG_FP64 = 0, STAG_FP32 = 1, STAG_FP16 = 2, STAG_FX16 = 3, STAG_DF64 = 4 } stag_prec;
 
-/* Solver modes.  PLAIN64: every operation in FP64.  MIXED32 / MIXED16 /
- * MIXEDFX16: the Krylov iteration uses the FP32 / binary16 / 16-bit
- * fixed-point Dslash and search direction, FP32 residual and iterate, FP64
- * reductions, FP64 solution accumulation and FP64 "reliable updates" (true
- * residual b - M y recomputed in FP64 whenever the iterated residual has
- * dropped by `delta` since the last update). */
+/* Solver modes (the paper: QUDA's mixed-precision solvers, Sec. 3; single
+ * precision about twice as fast as double, Sec. 4).  PLAIN64: every
+ * operation in FP64.  MIXED32 / MIXED16 / MIXEDFX16: the Krylov iteration
+ * uses the FP32 / binary16 / 16-bit fixed-point Dslash and search direction,
+ * FP32 residual and iterate, FP64-class reductions, FP64 solution
+ * accumulation and "reliable updates": the true residual b - M y recomputed
+ * with an FP64-class operator (STAG_DF64 if the handle holds that copy,
+ * else FP64) whenever the iterated residual has dropped by `delta` since the
+ * last update, and at the end. */
 typedef enum {
   STAG_PLAIN64 = 0,
   STAG_MIXED32 = 1,
@@ -80,7 +91,7 @@ typedef struct {
                         third rebuilt as conj(row0 x row1) (FP32 and 16-bit
                         copies; needs L/long_coeff in SU(3), else ENOTUNITARY) */
   double long_coeff; /* c3 with L = c3 * (product of SU(3) links); -1/24 */
-  unsigned prec_mask; /* bit (1 << stag_prec) per copy to build; 0 = all four */
+  unsigned prec_mask; /* bit (1 << stag_prec) per copy to build; 0 = all five */
   int autotune;      /* 1: time the Dslash launch shapes of each copy on this
                         lattice and keep the fastest (a few ms); 0: defaults */
 } stag_link_opts;
@@ -99,10 +110,11 @@ typedef struct {
 
 typedef struct {
   int iters;            /* Krylov iterations (multi-shift: shared + refinement) */
-  int reliable_updates; /* FP64 true-residual recomputations */
+  int reliable_updates; /* FP64-class true-residual recomputations */
   int converged;        /* 1 if true_rel_resid <= tol */
   int status;           /* STAG_OK or the error for this system */
-  double true_rel_resid; /* ||b - M x|| / ||b|| recomputed in FP64 on the GPU */
+  double true_rel_resid; /* ||b - M x|| / ||b|| recomputed on the GPU with the
+                            FP64-class operator of the reliable updates */
   double seconds;       /* wall time of the solve on the host */
   int precond_fallback; /* STAG_LEARNED: 1 if the mixed-CG fallback ran */
 } stag_solve_info;
@@ -132,23 +144,73 @@ int stag_free_lattice(stag_lattice_t lat);
 /* The launch shape the autotuner kept for a copy's Dslash kernel
  * (kernel 0: plain, 1: fused epilogue with dot product): threads per block,
  * minimum resident blocks per SM given to the compiler, and its timing in us
- * per launch (0 when not tuned).  Any output pointer may be NULL. */
+ * per launch (0 when not tuned).  For STAG_DF64 (four right-hand sides per
+ * launch) min_blocks reports the threads that share a site's right-hand
+ * sides (1, 2 or 4).  Any output pointer may be NULL. */
 int stag_tuned_shape(stag_lattice_t lat, int prec, int kernel, int* block, int* min_blocks, double* us);
+
+/* The launch variant of the N-right-hand-side Dslash kernels (the operator
+ * of stag_batch_solve and of stag_dslash with nrhs > 1) for groups of nrhs
+ * = 2, 4 or 8 right-hand sides of format prec on this lattice: the threads
+ * that share one site's right-hand sides (1, 2 or 4), the resident blocks
+ * per SM promised to the compiler (1: no register cap; 4: at most 128
+ * registers; 6: at most 80), and the timed cost of one operator application in us (0 when
+ * the variant was not timed: before the first such group, or with
+ * autotune off).  The variant is chosen, the first time a group of that
+ * size runs on a lattice of these extents, by timing every compiled variant
+ * (the autotuner; the paper tunes nothing at run time, its QPhiX and QUDA
+ * builds fix their blocking at compile time or tune it inside QUDA, Sec. 3).
+ * EINVAL for another nrhs or a missing copy.  Any output may be NULL. */
+int stag_tuned_mrhs(stag_lattice_t lat, int prec, int nrhs, int* threads_per_site, int* min_blocks, double* us);
+
+/* The autotuner's cache (host only, no GPU call).  Tuned launches are kept
+ * for the life of the process under a key naming the kernel family, the
+ * storage format, the Naik entries per hop, the right-hand sides per launch
+ * and the extents, e.g. "dslash_mrhs/fp32/nl6/n4/32x32x32x32"; a later
+ * lattice with the same key reuses the choice without timing.  If the
+ * environment variable STAG_TUNE_CACHE names a file, the cache is loaded
+ * from it on first use and the file is rewritten after every new entry.
+ * File format (JSON): {"version": 1, "entries": {"<key>": {"variant": v,
+ * "us": t}, ...}}.
+ *   stag_tune_key   : writes the key for (kernel, prec, nl, nrhs, dims) into
+ *                     buf (len bytes, NUL included); EINVAL if it does not fit
+ *   stag_tune_cache_get   : *variant = the stored variant, or -1 if the key
+ *                     is absent (*us likewise, 0)
+ *   stag_tune_cache_put   : stores (variant >= 0), replacing an entry
+ *   stag_tune_cache_load  : merges a file's entries; EINVAL if the file is
+ *                     missing or malformed (the cache is then unchanged)
+ *   stag_tune_cache_save  : writes every entry (via a temporary file)
+ *   stag_tune_cache_clear : forgets every entry (and the STAG_TUNE_CACHE file
+ *                     for the rest of the process)
+ *   stag_tune_cache_size  : number of entries */
+int stag_tune_key(char* buf, int len, const char* kernel, int prec, int nl, int nrhs, const int dims[4]);
+int stag_tune_cache_get(const char* key, int* variant, double* us);
+int stag_tune_cache_put(const char* key, int variant, double us);
+int stag_tune_cache_load(const char* path);
+int stag_tune_cache_save(const char* path);
+int stag_tune_cache_clear(void);
+long long stag_tune_cache_size(void);
 
 /* Lattice extents and the per-parity site count V/2 of a handle. */
 int stag_lattice_info(stag_lattice_t lat, int dims[4], long long* vh);
 
-/* out = D psi restricted to sites of parity out_parity (0 even, 1 odd);
- * in lives on the other parity.  Computed with the links and arithmetic of
- * `prec` (FP64: FP64 throughout; FP32: FP32 storage and accumulation; FP16
- * and FX16: 16-bit storage with a per-site vector scale and a per-field link
- * scale, FP32 accumulation).  in/out: device, canonical [nrhs][V/2][3] complex double
- * (converted to and from the internal layout around the kernel).
+/* out = D psi restricted to sites of parity out_parity (0 even, 1 odd); in
+ * lives on the other parity.  D is the operator written at the top of this
+ * header: the kernel of every CG iteration the paper benchmarks (Sec. 1,
+ * Sec. 4.1, its single-GPU L^4 sweep in Fig. 9), applied twice per
+ * iteration; the paper itself prints no formula for it.  Computed with the
+ * links and arithmetic of `prec` (FP64: FP64 throughout; DF64: double-float,
+ * see stag_prec; FP32: FP32 storage and accumulation; FP16 and FX16: 16-bit
+ * storage with a per-site vector scale and a per-field link scale, FP32
+ * accumulation).  nrhs > 1 right-hand sides share each link read (groups of
+ * 8, 4, 2; DF64: 4).  in/out: device, canonical [nrhs][V/2][3] complex
+ * double (converted to and from the internal layout around the kernel).
  * Asynchronous on `stream`.  Errors: EINVAL, ENOMEM, ECUDA. */
 int stag_dslash(stag_lattice_t lat, void* out, const void* in, int out_parity, int prec, int nrhs,
                 void* stream);
 
-/* out = (m^2 + shift) in - D_eo D_oe in on even sites, arithmetic of `prec`.
+/* out = (m^2 + shift) in - D_eo D_oe in on even sites, arithmetic of `prec`
+ * (the even-odd operator M whose solves the paper benchmarks, Sec. 4.1).
  * in/out: device canonical [V/2][3] complex double.  Asynchronous. */
 int stag_apply_m(stag_lattice_t lat, void* out, const void* in, double mass, double shift, int prec,
                  void* stream);
@@ -172,7 +234,11 @@ int stag_apply_m(stag_lattice_t lat, void* out, const void* in, double mass, dou
  *
  * The first call on a device looks up the array's device address for that
  * device (one-time set-up, with that device current); make that first call
- * before any stream capture.  All calls share the one array: calls whose
+ * before any stream capture.  The address is kept for the life of the
+ * device's context: do not use this call after cudaDeviceReset (or any
+ * other reset of the primary context) in the same process.  in and out
+ * must not overlap (STAG_EINVAL).  Profiler families "dslash64" and
+ * "dslash64_epi" (one launch each).  All calls share the one array: calls whose
  * kernels can overlap on the GPU (different streams, or several host
  * threads) race on it and must be serialised by the caller.  The array
  * keeps the last call's contents; nothing in it needs to start at zero, as
@@ -183,7 +249,10 @@ int stag_apply_m(stag_lattice_t lat, void* out, const void* in, double mass, dou
 int stag_apply_m_noalloc(stag_lattice_t lat, void* out, const void* in, double mass, double shift,
                          void* stream);
 
-/* Solve M x = b (even sites) to params->tol in FP64 true residual.
+/* Solve M x = b (even sites) to params->tol in FP64-class true residual:
+ * the single-mass CG of the paper (Sec. 1: the staggered QPhiX library
+ * provides single-mass and multi-shift CG; Sec. 4 and Fig. 1: CG takes
+ * about 90 % of the RHMD run time), with the precision modes of stag_mode.
  * x, b: device canonical [V/2][3] complex double; x is read as the initial
  * guess when params->use_initial_guess, and always written.
  * info: host, may be NULL.  Returns STAG_OK, ENOTCONV (x = last iterate),
@@ -211,23 +280,39 @@ typedef struct {
   double mass;
 } stag_batch_item;
 
-/* Solve every system of every item to params->tol (FP64 true residual), all
- * items together: each item's right-hand sides are solved in groups of up to
- * 8 that share one multi-right-hand-side Dslash per operator application
- * (links read once for the whole group), each system with its own CG
- * scalars and its own stopping point; the groups of all items advance side
- * by side, one CUDA graph launch per chunk of check_interval iterations.
- * Modes as for stag_cg (use_initial_guess reads x).  infos: host array with
- * one entry per system, item by item, may be NULL.  Returns STAG_OK, or the
- * first error (ENOTCONV, EBREAKDOWN ...) met by a system.  Synchronises
- * `stream`. */
+/* Solve every system of every item to params->tol (FP64-class true
+ * residual), all items together.  The paper solves one system at a time
+ * (Sec. 4.1) and says nothing of batching; this call is the library's
+ * extension for the many independent solves of a configuration (several
+ * sources, several gauge fields of uneven sizes).
+ * Each item's right-hand sides are solved in groups of up to 8 (16-bit
+ * modes: 4) that share one multi-right-hand-side Dslash per operator
+ * application (links read once for the whole group), each system with its
+ * own CG scalars and its own stopping point; a group takes a reliable update
+ * for all its systems when any of them triggers one.
+ *   - One group: chunks of check_interval iterations queued directly on the
+ *     group's stream, the host reading the group's state between chunks.
+ *   - Several groups: the whole solve is one launch of a CUDA graph whose
+ *     conditional WHILE node repeats a round over all groups side by side
+ *     (each group's reliable update when one is due, then check_interval
+ *     iterations whose kernels return at once once the group is done) until
+ *     every group is done or a fixed budget of rounds runs out; the host
+ *     waits once.
+ * Modes as for stag_cg except STAG_LEARNED (use_initial_guess reads x).
+ * infos: host array with one entry per system, item by item, may be NULL.
+ * Returns STAG_OK, or the first error (ENOTCONV, EBREAKDOWN ...) met by a
+ * system.  Synchronises `stream`. */
 int stag_batch_solve(const stag_batch_item* items, int nitems, const stag_solve_params* params,
                      stag_solve_info* infos, void* stream);
 
 /* ------------------------------------------------------------ learned part
- * A gauge-covariant network used as a preconditioner z = N(r) inside
- * flexible CG.  Fields are full-lattice, channels of colour vectors; a layer
- * with real weights W[d][c][c'] (stored as bfloat16, FP32 accumulation)
+ * The paper has no learned component: it benchmarks plain and multi-shift CG
+ * (Sec. 4.1).  These calls are the library's extension: a gauge-covariant
+ * network used as a preconditioner z = N(r) inside flexible CG (Notay's FCG
+ * with one-term truncation; STAG_LEARNED), trained on the GPU on (residual,
+ * error) pairs from the unpreconditioned solver.  Fields are full-lattice,
+ * channels of colour vectors; a layer with real weights W[d][c][c'] (stored
+ * as bfloat16, FP32 accumulation)
  * computes pre_c = sum_d sum_c' W[d][c][c'] T_d h_c', d = 0 the identity and
  * d = 1 + 2mu, 2 + 2mu the fat-link hops of the staggered operator from +mu
  * and -mu (the +-1/2 eta F parts of D); hidden layers apply the covariant
@@ -282,16 +367,19 @@ long long stag_net_num_params(stag_net_t net);
  * kernels use them (bfloat16 values), 0 the FP32 master copy */
 int stag_net_get_params(stag_net_t net, float* host, long long count, int rounded);
 int stag_net_set_params(stag_net_t net, const float* host, long long count);
-/* z = N(r), r and z device canonical [V/2][3] complex double.  Asynchronous. */
+/* z = N(r), r and z device canonical [V/2][3] complex double: the
+ * preconditioner application inside STAG_LEARNED flexible CG (no
+ * counterpart in the paper).  Asynchronous. */
 int stag_net_apply(stag_net_t net, stag_lattice_t lat, void* z, const void* r, void* stream);
 /* Loss of one pair (loss_kind: stag_loss; mass: the pair's m, used by
  * STAG_LOSS_RESIDUAL) and its gradient w.r.t. the parameters (host array of
- * count floats).  r, e: device canonical [V/2][3] complex double.
- * Synchronises `stream`. */
+ * count floats); no counterpart in the paper.  r, e: device canonical
+ * [V/2][3] complex double.  Synchronises `stream`. */
 int stag_net_loss_grad(stag_net_t net, stag_lattice_t lat, const void* r, const void* e, int loss_kind, double mass,
                        double* loss, float* grad, long long count, void* stream);
-/* Adam training on the pairs (all on lattices of one size); losses: host,
- * epochs * npairs values in visiting order, may be NULL.  Synchronises. */
+/* Adam training on the pairs (all on lattices of one size; no counterpart in
+ * the paper); losses: host, epochs * npairs values in visiting order, may be
+ * NULL.  Synchronises. */
 int stag_net_train(stag_net_t net, const stag_train_pair* pairs, int npairs, const stag_train_params* tp,
                    double* losses, void* stream);
 
@@ -369,7 +457,8 @@ const char* stag_strerror(int status);
  * time (ms).  Families: "dslash", "dslash_epi" (FP32 and 16-bit operator,
  * plain and with the fused axpy/reduction epilogue), "dslash64",
  * "dslash64_epi" (FP64), "dslash_mrhs", "dslash_mrhs_epi", "dslash_mrhs64",
- * "dslash_mrhs64_epi" (multi-right-hand-side forms), "blas", "reduce",
+ * "dslash_mrhs64_epi" (multi-right-hand-side forms), "dslash_df",
+ * "dslash_df_epi" (double-float), "blas", "reduce",
  * "convert", "links", "net", "net_bwd", "gauge_force", "fermion_force".  stag_launch_count
  * counts all library kernel launches since the last reset, whether or not
  * profiling is on. */
@@ -377,7 +466,11 @@ int stag_profile_enable(int on);
 /* Restrict the event pairs to the listed families (comma-separated, e.g.
  * "dslash,dslash_epi"; NULL or "" times every family) and to one launch in
  * `every` of each family (every <= 1: all), which keeps the events' own cost
- * out of the measured workload. */
+ * out of the measured workload.  With every > 1 the solvers drop the samples
+ * of a chunk of queued iterations that a stop flag (a reliable-update
+ * trigger, convergence) cut short, whose later launches return at once: the
+ * sampled averages then time launches that did their work.  With every <= 1
+ * all launches count. */
 int stag_profile_select(const char* families, int every);
 /* Zero every family's launch count and time, and the launch counter. */
 int stag_profile_reset(void);

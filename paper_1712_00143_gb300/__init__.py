@@ -30,10 +30,10 @@ STAG_EBREAKDOWN = -5
 STAG_ENOTUNITARY = -6
 STAG_ETIMEOUT = -7
 
-STAG_FP64, STAG_FP32, STAG_FP16, STAG_FX16 = 0, 1, 2, 3
+STAG_FP64, STAG_FP32, STAG_FP16, STAG_FX16, STAG_DF64 = 0, 1, 2, 3, 4
 STAG_PLAIN64, STAG_MIXED32, STAG_MIXED16, STAG_MIXEDFX16, STAG_LEARNED = 0, 1, 2, 3, 4
 
-PREC = {"fp64": STAG_FP64, "fp32": STAG_FP32, "fp16": STAG_FP16, "fx16": STAG_FX16}
+PREC = {"fp64": STAG_FP64, "fp32": STAG_FP32, "fp16": STAG_FP16, "fx16": STAG_FX16, "df64": STAG_DF64}
 MODE = {
     "plain64": STAG_PLAIN64,
     "mixed32": STAG_MIXED32,
@@ -73,6 +73,14 @@ EXPORTS = (
     "stag_profile_reset",
     "stag_profile_read",
     "stag_launch_count",
+    "stag_tuned_mrhs",
+    "stag_tune_key",
+    "stag_tune_cache_get",
+    "stag_tune_cache_put",
+    "stag_tune_cache_load",
+    "stag_tune_cache_save",
+    "stag_tune_cache_clear",
+    "stag_tune_cache_size",
 )
 
 
@@ -192,6 +200,14 @@ def load_library(path=LIB_PATH):
         "stag_profile_reset": (ci, []),
         "stag_profile_read": (ci, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(cd)]),
         "stag_launch_count": (ctypes.c_longlong, []),
+        "stag_tuned_mrhs": (ci, [vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(cd)]),
+        "stag_tune_key": (ci, [ctypes.c_char_p, ci, ctypes.c_char_p, ci, ci, ci, ctypes.POINTER(ci)]),
+        "stag_tune_cache_get": (ci, [ctypes.c_char_p, ctypes.POINTER(ci), ctypes.POINTER(cd)]),
+        "stag_tune_cache_put": (ci, [ctypes.c_char_p, ci, cd]),
+        "stag_tune_cache_load": (ci, [ctypes.c_char_p]),
+        "stag_tune_cache_save": (ci, [ctypes.c_char_p]),
+        "stag_tune_cache_clear": (ci, []),
+        "stag_tune_cache_size": (ctypes.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -568,3 +584,46 @@ def stag_profile_read(family):
 
 def stag_launch_count():
     return int(_lib.stag_launch_count())
+
+
+def stag_tuned_mrhs(h, prec, nrhs):
+    """(threads per site, min blocks per SM, us per operator application) of
+    the N-right-hand-side kernels' tuned launch variant (us 0: not timed)."""
+    t, m, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(_lib.stag_tuned_mrhs(h.ptr, _prec(prec), int(nrhs), ctypes.byref(t), ctypes.byref(m), ctypes.byref(us)),
+           "stag_tuned_mrhs")
+    return t.value, m.value, us.value
+
+
+def stag_tune_key(kernel, prec, nl, nrhs, dims):
+    buf = ctypes.create_string_buffer(256)
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    _check(_lib.stag_tune_key(buf, 256, kernel.encode(), _prec(prec), int(nl), int(nrhs), d), "stag_tune_key")
+    return buf.value.decode()
+
+
+def stag_tune_cache_get(key):
+    """(variant, us) stored under key, or (-1, 0.0)."""
+    v, us = ctypes.c_int(), ctypes.c_double()
+    _check(_lib.stag_tune_cache_get(key.encode(), ctypes.byref(v), ctypes.byref(us)), "stag_tune_cache_get")
+    return v.value, us.value
+
+
+def stag_tune_cache_put(key, variant, us):
+    _check(_lib.stag_tune_cache_put(key.encode(), int(variant), float(us)), "stag_tune_cache_put")
+
+
+def stag_tune_cache_load(path):
+    _check(_lib.stag_tune_cache_load(os.fsencode(path)), "stag_tune_cache_load")
+
+
+def stag_tune_cache_save(path):
+    _check(_lib.stag_tune_cache_save(os.fsencode(path)), "stag_tune_cache_save")
+
+
+def stag_tune_cache_clear():
+    _check(_lib.stag_tune_cache_clear(), "stag_tune_cache_clear")
+
+
+def stag_tune_cache_size():
+    return int(_lib.stag_tune_cache_size())

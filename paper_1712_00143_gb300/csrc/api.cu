@@ -73,6 +73,7 @@ namespace {
 struct Rec {
   const char* family;
   cudaEvent_t a, b;
+  long long seq;  // creation order (see prof_discard_since)
 };
 std::mutex g_mu;
 bool g_prof = false;
@@ -87,6 +88,7 @@ struct Tot {
   double ms = 0.0;
 };
 std::map<std::string, Tot> g_tot;
+long long g_seq = 0;
 thread_local int t_pending = -1;
 
 cudaEvent_t take_event() {
@@ -174,7 +176,7 @@ void prof_begin(const char* family, cudaStream_t s) {
   cudaEvent_t a = take_event();
   if (!a) return;
   cudaEventRecord(a, s);
-  g_open.push_back(Rec{family, a, nullptr});
+  g_open.push_back(Rec{family, a, nullptr, g_seq++});
   t_pending = (int)g_open.size() - 1;
 }
 
@@ -193,6 +195,37 @@ void prof_flush_completed() {
   if (!g_prof) return;
   std::lock_guard<std::mutex> lk(g_mu);
   flush_locked(false);
+}
+
+long long prof_mark() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_seq;
+}
+
+// Drops the records created since `mark` that have not been accumulated yet,
+// when launches are sampled (every > 1; with every launch timed the totals
+// stay complete).  The solvers call it, before their next
+// prof_flush_completed, for a chunk of queued iterations that a stop flag
+// cut short: the launches queued after the flag returned at once and would
+// otherwise enter the sampled averages as near-empty launches.  (Records are
+// accumulated only by an explicit flush, or when more than 8192 are open,
+// far above the records of one chunk.)
+void prof_discard_since(long long mark) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_every <= 1) return;
+  size_t keep = 0;
+  for (size_t i = 0; i < g_open.size(); ++i) {
+    Rec& r = g_open[i];
+    if (r.seq >= mark) {
+      if (r.b) cudaEventSynchronize(r.b);
+      cudaGetLastError();
+      g_pool.push_back(r.a);
+      if (r.b) g_pool.push_back(r.b);
+    } else {
+      g_open[keep++] = r;
+    }
+  }
+  g_open.resize(keep);
 }
 
 }  // namespace stag
@@ -280,17 +313,19 @@ int stag_load_links(stag_lattice_t* out, const int dims[4], const void* fat, con
   if (opts) o = *opts;
   if (o.recon_long != 18 && o.recon_long != 12) return STAG_EINVAL;
   if (o.recon_long == 12 && !(o.long_coeff != 0.0)) return STAG_EINVAL;
-  unsigned mask = o.prec_mask ? o.prec_mask : 15u;
-  if (mask & ~15u) return STAG_EINVAL;
+  unsigned mask = o.prec_mask ? o.prec_mask : 31u;
+  if (mask & ~31u) return STAG_EINVAL;
   stag_lattice_s* lat = new stag_lattice_s();
   for (int i = 0; i < 4; ++i) lat->dims[i] = dims[i];
   lat->g = make_geom(dims);
   lat->c3 = o.long_coeff;
+  lat->autotune = o.autotune ? 1 : 0;
   cudaStream_t st = (cudaStream_t)stream;
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < 5; ++p) {
     if (!((mask >> p) & 1)) continue;
     int s = build_link_copy(lat, p, o.recon_long, (const double2*)fat, (const double2*)lng, st);
-    if (!s && o.autotune) {
+    if (!s && o.autotune && p == STAG_DF64) s = tune_df(lat, st);
+    if (!s && o.autotune && p != STAG_DF64) {
       switch (p) {
         case STAG_FP64: s = tune_dslash<64>(lat, st); break;
         case STAG_FP32: s = tune_dslash<32>(lat, st); break;
@@ -317,9 +352,17 @@ int stag_free_lattice(stag_lattice_t lat) {
 }
 
 int stag_tuned_shape(stag_lattice_t lat, int prec, int kernel, int* block, int* min_blocks, double* us) {
-  if (!lat || prec < 0 || prec > 3 || kernel < 0 || kernel > 1 || !lat->links[prec].present) return STAG_EINVAL;
+  if (!lat || prec < 0 || prec > 4 || kernel < 0 || kernel > 1 || !lat->links[prec].present) return STAG_EINVAL;
   const LinkCopy& L = lat->links[prec];
   int v = kernel == 0 ? L.shape_plain : L.shape_epi;
+  if (prec == STAG_DF64) {
+    // double-float: 128 threads per block; min_blocks reports the threads
+    // that share one site's four right-hand sides (1, 2 or 4)
+    if (block) *block = 128;
+    if (min_blocks) *min_blocks = v == 0 ? 1 : v == 1 ? 2 : 4;
+    if (us) *us = L.tuned_us[kernel];
+    return STAG_OK;
+  }
   if (block) *block = v < 2 ? 256 : 128;
   if (min_blocks) *min_blocks = v == 1 ? 4 : v == 3 ? 8 : 1;
   if (us) *us = L.tuned_us[kernel];
@@ -386,14 +429,41 @@ static int apply_m_p(stag_lattice_s* lat, double2* out, const double2* in, doubl
   return launch_to_canonical<PA>(out, o, lat->g.Vh, st);
 }
 
+// Double-float: canonical FP64 in, split exactly, DF hops, DF out widened to FP64.
+static int dslash_df_canonical(stag_lattice_s* lat, double2* out, const double2* in, int out_parity, int nrhs,
+                               cudaStream_t st) {
+  int s = 0;
+  const int Vh = lat->g.Vh;
+  DfField a{(float4*)lat->ws.get("dslashdf.in", df_bytes(Vh) * nrhs, &s), Vh};
+  DfField b{(float4*)lat->ws.get("dslashdf.out", df_bytes(Vh) * nrhs, &s), Vh};
+  if (s) return s;
+  if ((s = launch_df_from_double(a, in, nrhs, st))) return s;
+  if ((s = launch_dslash_df(lat, b, a, nrhs, out_parity, nullptr, st))) return s;
+  return launch_df_to_double(out, b, nrhs, st);
+}
+
+static int apply_m_df(stag_lattice_s* lat, double2* out, const double2* in, double shift, cudaStream_t st) {
+  int s = 0;
+  const int Vh = lat->g.Vh;
+  DfField a{(float4*)lat->ws.get("applymdf.in", df_bytes(Vh), &s), Vh};
+  DfField t{(float4*)lat->ws.get("applymdf.t", df_bytes(Vh), &s), Vh};
+  DfField o{(float4*)lat->ws.get("applymdf.out", df_bytes(Vh), &s), Vh};
+  if (s) return s;
+  if ((s = launch_df_from_double(a, in, 1, st))) return s;
+  if ((s = launch_dslash_df(lat, t, a, 1, 1, nullptr, st))) return s;
+  if ((s = launch_dslash_df_epi(lat, o, t, 1, 0, a, shift, DfField{nullptr, Vh}, 0.0, -1.0, nullptr, st))) return s;
+  return launch_df_to_double(out, o, 1, st);
+}
+
 }  // namespace stag
 
 extern "C" {
 
 int stag_dslash(stag_lattice_t lat, void* out, const void* in, int out_parity, int prec, int nrhs, void* stream) {
   if (!lat || !out || !in || (out_parity != 0 && out_parity != 1) || nrhs < 1) return STAG_EINVAL;
-  if (prec < 0 || prec > 3 || !lat->links[prec].present) return STAG_EINVAL;
+  if (prec < 0 || prec > 4 || !lat->links[prec].present) return STAG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  if (prec == STAG_DF64) return dslash_df_canonical(lat, (double2*)out, (const double2*)in, out_parity, nrhs, st);
   if (nrhs > 1) return dslash_multi(lat, (double2*)out, (const double2*)in, out_parity, prec, nrhs, st);
   switch (prec) {
     case STAG_FP64: return dslash_p<64>(lat, (double2*)out, (const double2*)in, out_parity, nrhs, st);
@@ -405,9 +475,10 @@ int stag_dslash(stag_lattice_t lat, void* out, const void* in, int out_parity, i
 
 int stag_apply_m(stag_lattice_t lat, void* out, const void* in, double mass, double shift, int prec, void* stream) {
   if (!lat || !out || !in) return STAG_EINVAL;
-  if (prec < 0 || prec > 3 || !lat->links[prec].present) return STAG_EINVAL;
+  if (prec < 0 || prec > 4 || !lat->links[prec].present) return STAG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   double a = mass * mass + shift;
+  if (prec == STAG_DF64) return apply_m_df(lat, (double2*)out, (const double2*)in, a, st);
   switch (prec) {
     case STAG_FP64: return apply_m_p<64>(lat, (double2*)out, (const double2*)in, a, st);
     case STAG_FP32: return apply_m_p<32>(lat, (double2*)out, (const double2*)in, a, st);

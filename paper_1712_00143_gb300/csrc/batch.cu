@@ -54,69 +54,7 @@ int grid_bw(int Vh) {
   return g < m ? g : m;
 }
 
-template <int P> DslashArgsM<P> make_args_m(const stag_lattice_s* lat, SpinorM<P> in, int out_parity) {
-  const LinkCopy& L = lat->links[prec_index<P>()];
-  DslashArgsM<P> a;
-  a.g = lat->g;
-  a.out_parity = out_parity;
-  a.links = (const uint4*)((const char*)L.data + (size_t)out_parity * L.parity_stride);
-  const double fx = P == 15 ? 1.0 / 32767.0 : 1.0;
-  a.fat_scale = (float)(L.fat_scale * fx);
-  a.long_scale = (float)((L.nl == 6 ? 0.5 * lat->c3 : (double)L.long_scale) * fx);
-  a.in = in;
-  return a;
-}
-
 }  // namespace
-
-template <int P, int N>
-int mdslash(const stag_lattice_s* lat, SpinorM<P> out, SpinorM<P> in, int out_parity, const int* flags,
-            cudaStream_t st) {
-  const LinkCopy& L = lat->links[prec_index<P>()];
-  if (!L.present) return STAG_EINVAL;
-  DslashArgsM<P> a = make_args_m<P>(lat, in, out_parity);
-  const int G = (lat->g.Vh + MB - 1) / MB;
-  ProfScope ps(P == 64 ? "dslash_mrhs64" : "dslash_mrhs", st);
-  constexpr int NL6 = P == 64 ? 9 : 6;
-  if constexpr (mrhs_capped(P, N)) {
-    if (L.nl == 9)
-      k_dslash_m_cap<P, 9, N><<<G, MB, 0, st>>>(a, out, flags);
-    else
-      k_dslash_m_cap<P, NL6, N><<<G, MB, 0, st>>>(a, out, flags);
-  } else {
-    if (P == 64 || L.nl == 9)
-      k_dslash_m<P, 9, N><<<G, MB, 0, st>>>(a, out, flags);
-    else
-      k_dslash_m<P, NL6, N><<<G, MB, 0, st>>>(a, out, flags);
-  }
-  return last_launch_status();
-}
-
-template <int P, int N, int RED>
-int mdslash_epi(const stag_lattice_s* lat, SpinorM<Acc<P>::value> out, SpinorM<P> in, int out_parity, SpinorM<P> x,
-                double ax, SpinorM<Acc<P>::value> y, double ay, double ad, RedScratch rs, RedTarget tgt,
-                const int* flags, cudaStream_t st) {
-  const LinkCopy& L = lat->links[prec_index<P>()];
-  if (!L.present) return STAG_EINVAL;
-  DslashArgsM<P> a = make_args_m<P>(lat, in, out_parity);
-  const int G = (lat->g.Vh + MB - 1) / MB;
-  if (RED && G > rs.max_grid) return STAG_EINVAL;
-  ProfScope ps(P == 64 ? "dslash_mrhs64_epi" : "dslash_mrhs_epi", st);
-  RedBuf rb{rs.partials, rs.counter};
-  constexpr int NL6 = P == 64 ? 9 : 6;
-  if constexpr (mrhs_capped(P, N)) {
-    if (L.nl == 9)
-      k_dslash_m_epi_cap<P, 9, N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
-    else
-      k_dslash_m_epi_cap<P, NL6, N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
-  } else {
-    if (P == 64 || L.nl == 9)
-      k_dslash_m_epi<P, 9, N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
-    else
-      k_dslash_m_epi<P, NL6, N, RED><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
-  }
-  return last_launch_status();
-}
 
 template <int P> SpinorM<P> ws_spinorm(stag_lattice_s* lat, const std::string& name, int n, int* status) {
   SpinorM<P> f;
@@ -129,7 +67,8 @@ template <int P> SpinorM<P> ws_spinorm(stag_lattice_s* lat, const std::string& n
 // ------------------------------------------------------------ stag_dslash, nrhs > 1
 template <int P, int N>
 static int dslash_group(stag_lattice_s* lat, double2* out, const double2* in, int out_parity, cudaStream_t st) {
-  int s = 0;
+  int s = tune_mrhs<P, N>(lat, st);
+  if (s) return s;
   SpinorM<P> a = ws_spinorm<P>(lat, "mdslash.in", N, &s);
   SpinorM<P> b = ws_spinorm<P>(lat, "mdslash.out", N, &s);
   if (s) return s;
@@ -196,6 +135,10 @@ struct GroupBase {
   virtual int start(const stag_solve_params& prm) = 0;
   virtual int iterations(int C) = 0;
   virtual int reliable_update() = 0;
+  // the same update with the FP64 operator: the final verdict on a group
+  // whose double-float residual reached the target
+  virtual int reliable_update_fp64() = 0;
+  virtual bool uses_df() const = 0;
   virtual int round_dev(int C) = 0;
   virtual int finish() = 0;
 };
@@ -205,31 +148,57 @@ template <int P, int N> struct Group : GroupBase {
   SpinorM<64> b64, y64, r64, t64;
   SpinorM<P> p, t;
   SpinorM<PV> Ap, xh, rh;
+  // reliable updates in double-float (when the handle holds that link copy):
+  // the anchor (ya64, its residual radf; see McgState), y - ya, the odd
+  // intermediate and the residual
+  bool use_df = false;
+  SpinorM<64> ya64;
+  DfField radf, ydf, tdf, rdf;
   RedScratch rs;
   int n() const override { return N; }
+  bool uses_df() const override { return use_df; }
 
   int alloc(int gid) {
-    int s = 0;
+    // the launch variant of this group's operator kernels (timed once per
+    // format, N and lattice shape)
+    int s = tune_mrhs<P, N>(lat, st);
+    if (s) return s;
     const std::string pre = "batch" + std::to_string(gid) + ".";
     b64 = ws_spinorm<64>(lat, pre + "b", N, &s);
     y64 = ws_spinorm<64>(lat, pre + "y", N, &s);
-    r64 = ws_spinorm<64>(lat, pre + "r64", N, &s);
-    t64 = ws_spinorm<64>(lat, pre + "t64", N, &s);
     p = ws_spinorm<P>(lat, pre + "p", N, &s);
     t = ws_spinorm<P>(lat, pre + "t", N, &s);
     Ap = ws_spinorm<PV>(lat, pre + "Ap", N, &s);
     xh = ws_spinorm<PV>(lat, pre + "xh", N, &s);
     rh = ws_spinorm<PV>(lat, pre + "rh", N, &s);
+    use_df = P != 64 && lat->links[STAG_DF64].present;
+    const int Vh = lat->g.Vh;
+    if (use_df) {
+      ya64 = ws_spinorm<64>(lat, pre + "ya", N, &s);
+      radf = DfField{(float4*)lat->ws.get(pre + "radf", df_bytes(Vh) * N, &s), Vh};
+      ydf = DfField{(float4*)lat->ws.get(pre + "ydf", df_bytes(Vh) * N, &s), Vh};
+      tdf = DfField{(float4*)lat->ws.get(pre + "tdf", df_bytes(Vh) * N, &s), Vh};
+      rdf = DfField{(float4*)lat->ws.get(pre + "rdf", df_bytes(Vh) * N, &s), Vh};
+    }
+    t64 = ws_spinorm<64>(lat, pre + "t64", N, &s);
+    r64 = ws_spinorm<64>(lat, pre + "r64", N, &s);
     dst = (McgState*)lat->ws.get(pre + "state", sizeof(McgState), &s);
     dscal = (double*)lat->ws.get(pre + "scal", sizeof(double) * 2 * MAX_RHS, &s);
     if (s) return s;
-    return get_red_scratch(lat, (pre + "red").c_str(), &rs, 2 * N);
+    return get_red_scratch(lat, (pre + "red").c_str(), &rs, 3 * N);
   }
 
   // FP64: r = b - shift y + D_eo D_oe y, ||r_i||^2 -> tgt (stop: a stop word, or nullptr)
   int true_residual(RedTarget tgt, const int* stop = nullptr) {
     TRYB((mdslash<64, N>(lat, t64, y64, 1, stop, st)));
     return mdslash_epi<64, N, 2>(lat, r64, t64, 0, y64, -shift, b64, 1.0, 1.0, rs, tgt, stop, st);
+  }
+
+  // Double-float: rdf = r_a - M (y - y_a) = radf - shift ydf + D_eo D_oe ydf
+  // (ydf = y - y_a), no reduction
+  int true_residual_df(const int* stop) {
+    TRYB(launch_dslash_df(lat, tdf, ydf, N, 1, stop, st));
+    return launch_dslash_df_epi(lat, rdf, tdf, N, 0, ydf, -shift, radf, 1.0, 1.0, stop, st);
   }
 
   int setup(const stag_solve_params& prm) override {
@@ -244,13 +213,24 @@ template <int P, int N> struct Group : GroupBase {
                                                                          RedTarget{RED_STORE, nullptr, dscal});
     }
     TRYB(last_launch_status());
+    if (use_df) {
+      // the anchor starts at (0, b)
+      TRYB(launch_df_from_double(radf, (const double2*)b64.v, N, st));
+      TRYB(cuda_status(cudaMemsetAsync(ya64.v, 0, spinorm_bytes<64>(lat->g.Vh, N), st)));
+    }
     if (prm.use_initial_guess) {
       {
         ProfScope ps("convert", st);
         k_mfrom_canonical<64, N><<<grid_bw(lat->g.Vh), 256, 0, st>>>(y64, x, nreal);
       }
       TRYB(last_launch_status());
-      TRYB(true_residual(RedTarget{RED_STORE, nullptr, dscal + MAX_RHS}));
+      if (use_df) {
+        TRYB(launch_df_from_double(ydf, (const double2*)y64.v, N, st));
+        TRYB(true_residual_df(nullptr));
+        TRYB(launch_norm2_df(rdf, N, rs, RedTarget{RED_STORE, nullptr, dscal + MAX_RHS}, st));
+      } else {
+        TRYB(true_residual(RedTarget{RED_STORE, nullptr, dscal + MAX_RHS}));
+      }
     } else {
       TRYB(cuda_status(cudaMemsetAsync(y64.v, 0, spinorm_bytes<64>(lat->g.Vh, N), st)));
       TRYB(cuda_status(cudaMemcpyAsync(r64.v, b64.v, spinorm_bytes<64>(lat->g.Vh, N), cudaMemcpyDeviceToDevice, st)));
@@ -282,14 +262,22 @@ template <int P, int N> struct Group : GroupBase {
     h.status = STAG_OK;
     h.ru_skip = F_CONVERGED;
     h.skip_xpay = 1;
+    h.use_df = use_df ? 1 : 0;
+    h.anchored = 0;
+    h.ru_skip64 = F_CONVERGED;
+    for (int i = 0; i < N; ++i) h.anchor_rr[i] = kDfAnchorRel2 * bb[i];
     *hst = h;
     TRYB(cuda_status(cudaMemcpyAsync(dst, hst, sizeof(McgState), cudaMemcpyHostToDevice, st)));
     const int G = grid_bw(lat->g.Vh);
-    {
-      ProfScope ps("convert", st);
-      k_mconvert<PV, 64, N><<<G, 256, 0, st>>>(rh, r64);
+    if (use_df && prm.use_initial_guess) {
+      TRYB(launch_convert_from_df<PV>(rh.v, rdf, N, st));
+    } else {
+      {
+        ProfScope ps("convert", st);
+        k_mconvert<PV, 64, N><<<G, 256, 0, st>>>(rh, r64);
+      }
+      TRYB(last_launch_status());
     }
-    TRYB(last_launch_status());
     TRYB(cuda_status(cudaMemsetAsync(xh.v, 0, spinorm_bytes<PV>(lat->g.Vh, N), st)));
     {
       ProfScope ps("convert", st);
@@ -334,24 +322,51 @@ template <int P, int N> struct Group : GroupBase {
     return STAG_OK;
   }
 
-  int reliable_update() override { return ru_kernels(nullptr); }
+  // Host-driven update: double-float, or the FP64 update that moves the
+  // anchor when every active system's residual has fallen below its level.
+  int reliable_update() override {
+    bool anchor = use_df && !hst->anchored;
+    for (int i = 0; i < N && anchor; ++i)
+      if (((hst->active >> i) & 1) && !(hst->sys[i].rr < hst->anchor_rr[i])) anchor = false;
+    if (use_df && !anchor) return ru_kernels(nullptr, true);
+    return reliable_update_fp64();
+  }
+  int reliable_update_fp64() override {
+    TRYB(ru_kernels(nullptr, false));
+    if (!use_df) return STAG_OK;
+    TRYB(launch_df_anchor(ya64.v, radf, y64.v, r64.v, N, nullptr, st));
+    hst->anchored = 1;
+    return cuda_status(cudaMemcpyAsync(&dst->anchored, &hst->anchored, sizeof(int), cudaMemcpyHostToDevice, st));
+  }
 
-  // the update's kernels; with stop = &dst->ru_skip they run only when a
-  // reliable update is due (graph-resident loop)
-  int ru_kernels(const int* stop) {
+  // the update's kernels (df: double-float operator, else FP64); with
+  // stop = &dst->ru_skip they run only when a reliable update is due
+  // (graph-resident loop)
+  int ru_kernels(const int* stop, bool df) {
     const int Vh = lat->g.Vh;
-    {
-      ProfScope ps("blas", st);
-      k_maccumulate<PV, N><<<grid_bw(Vh), 256, 0, st>>>(y64, xh, stop);
+    if constexpr (P != 64) {
+      if (df) {
+        // y += xh in FP64 (and its DF copy), r = b - M y in double-float,
+        // rh = r with ||rh||^2 and <rh, p> in one pass
+        TRYB(launch_accumulate_df<PV>(y64.v, xh.v, ydf, ya64.v, N, stop, st));
+        TRYB(true_residual_df(stop));
+        TRYB(launch_ru_convert_dot_df<P>(rh.v, rdf, p.v, N, rs, RedTarget{RED_MCG_RU_BOTH, dst, nullptr}, stop, st));
+      }
     }
-    TRYB(last_launch_status());
-    TRYB(true_residual(RedTarget{RED_MCG_RU_RESID, dst, nullptr}, stop));
-    {
-      ProfScope ps("reduce", st);
-      k_mru_convert_dot<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(rh, r64, p, dst,
-                                                                          RedBuf{rs.partials, rs.counter}, stop);
+    if (!df) {
+      {
+        ProfScope ps("blas", st);
+        k_maccumulate<PV, N><<<grid_bw(Vh), 256, 0, st>>>(y64, xh, stop);
+      }
+      TRYB(last_launch_status());
+      TRYB(true_residual(RedTarget{RED_MCG_RU_RESID, dst, nullptr}, stop));
+      {
+        ProfScope ps("reduce", st);
+        k_mru_convert_dot<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(rh, r64, p, dst,
+                                                                            RedBuf{rs.partials, rs.counter}, stop);
+      }
+      TRYB(last_launch_status());
     }
-    TRYB(last_launch_status());
     {
       ProfScope ps("blas", st);
       k_mru_p<P, N><<<grid_bw(Vh), 256, 0, st>>>(p, rh, dst, stop);
@@ -371,7 +386,13 @@ template <int P, int N> struct Group : GroupBase {
     count_launch();
     k_mcg_ru_gate<<<1, 1, 0, st>>>(dst);
     TRYB(last_launch_status());
-    TRYB(ru_kernels(&dst->ru_skip));
+    if (use_df) {
+      TRYB(ru_kernels(&dst->ru_skip, true));
+      TRYB(ru_kernels(&dst->ru_skip64, false));
+      TRYB(launch_df_anchor(ya64.v, radf, y64.v, r64.v, N, &dst->ru_skip64, st));
+    } else {
+      TRYB(ru_kernels(&dst->ru_skip64, false));
+    }
     count_launch();
     k_mcg_ru_decide<<<1, 1, 0, st>>>(dst);
     TRYB(last_launch_status());
@@ -622,8 +643,25 @@ static int batch_solve_p(const stag_batch_item* items, int nitems, const stag_so
       if (g->hst->done == 0) g->status = STAG_ENOTCONV;  // the round budget ran out
       else g->status = g->hst->status;
     }
+    // the FP64 verdict on the groups retired by their double-float residual;
+    // a group it finds short of the target iterates on in the host loop
+    std::vector<GroupBase*> verdict;
+    for (auto& g : groups)
+      if (g->uses_df() && g->status == STAG_OK && g->hst->active == 0) verdict.push_back(g.get());
+    for (GroupBase* g : verdict) TRYB(g->reliable_update_fp64());
+    for (GroupBase* g : verdict)
+      TRYB(cuda_status(cudaMemcpyAsync(g->hst, g->dst, sizeof(McgState), cudaMemcpyDeviceToHost, g->st)));
+    for (GroupBase* g : verdict) {
+      TRYB(cuda_status(cudaStreamSynchronize(g->st)));
+      if (g->hst->flags & F_BREAKDOWN) {
+        g->status = STAG_EBREAKDOWN;
+      } else if (g->hst->active != 0) {
+        g->done = false;
+        g->pending_p = false;
+      }
+    }
   }
-  for (; ng == 1;) {
+  for (;;) {
     std::vector<int> live;
     for (int k = 0; k < ng; ++k)
       if (!groups[k]->done) live.push_back(k);
@@ -638,6 +676,7 @@ static int batch_solve_p(const stag_batch_item* items, int nitems, const stag_so
     // stays ahead of the GPU, so the chunk is queued directly (and the
     // library's per-launch profiler can time it); graphs pay off when
     // several groups run side by side
+    const long long mark = prof_mark();
     if (!steady || ng == 1) {
       // first chunk after a start or a reliable update: queue directly
       for (int k : live) TRYB(groups[k]->iterations(C));
@@ -683,6 +722,11 @@ static int batch_solve_p(const stag_batch_item* items, int nitems, const stag_so
       TRYB(cuda_status(cudaMemcpyAsync(g.hst, g.dst, sizeof(McgState), cudaMemcpyDeviceToHost, g.st)));
     }
     for (int k : live) TRYB(cuda_status(cudaStreamSynchronize(groups[k]->st)));
+    // a chunk in which a stop flag was raised holds launches that returned at
+    // once: its profiling records would not time the kernels' work
+    bool cut = false;
+    for (int k : live) cut = cut || (groups[k]->hst->flags & F_STOP);
+    if (cut) prof_discard_since(mark);
     prof_flush_completed();
     std::vector<int> ru;
     for (int k : live) {
@@ -696,6 +740,18 @@ static int batch_solve_p(const stag_batch_item* items, int nitems, const stag_so
     }
     for (int k : ru) TRYB(groups[k]->reliable_update());
     for (int k : ru) {
+      GroupBase& g = *groups[k];
+      TRYB(cuda_status(cudaMemcpyAsync(g.hst, g.dst, sizeof(McgState), cudaMemcpyDeviceToHost, g.st)));
+    }
+    // a double-float residual at the target is judged once more in FP64
+    std::vector<int> verdict;
+    for (int k : ru) {
+      GroupBase& g = *groups[k];
+      TRYB(cuda_status(cudaStreamSynchronize(g.st)));
+      if (g.uses_df() && !(g.hst->flags & F_BREAKDOWN) && g.hst->active == 0) verdict.push_back(k);
+    }
+    for (int k : verdict) TRYB(groups[k]->reliable_update_fp64());
+    for (int k : verdict) {
       GroupBase& g = *groups[k];
       TRYB(cuda_status(cudaMemcpyAsync(g.hst, g.dst, sizeof(McgState), cudaMemcpyDeviceToHost, g.st)));
     }

@@ -1,109 +1,12 @@
-// batch_kernels.cuh -- kernels of the multi-right-hand-side CG: the N-RHS
-// Dslash (plain and with the fused axpy and per-system FP64 reductions) and
-// the per-system level-1 kernels, all on the MRHS layout of dslash_mrhs.cuh.
-// Each system i of a group reads its own scalars (alpha_i, beta_i ...) from
-// the group's McgState.
+// batch_kernels.cuh -- kernels of the multi-right-hand-side CG: the
+// per-system level-1 kernels and the control kernels of the graph-resident
+// loop, all on the MRHS layout of dslash_mrhs.cuh (the N-RHS Dslash kernels
+// are in mrhs_kernels.cuh).  Each system i of a group reads its own scalars
+// (alpha_i, beta_i ...) from the group's McgState.
 #pragma once
 #include "dslash_mrhs.cuh"
 
 namespace stag {
-
-constexpr int MB = 128;  // threads per block of the N-RHS kernels
-template <int P, int NL, int N>
-__device__ __forceinline__ void dslash_m_body(const DslashArgsM<P>& a, SpinorM<P> out, const int* flags) {
-  if (stopped(flags)) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.g.Vh) return;
-  typename Prec<P>::A2 d[N][3];
-  dslash_site_m<P, NL, N>(a, s, d);
-#pragma unroll
-  for (int r = 0; r < N; ++r) SpinorLoadM<P>::st(out, s, r, d[r]);
-}
-
-template <int P, int NL, int N>
-__global__ void __launch_bounds__(MB) k_dslash_m(DslashArgsM<P> a, SpinorM<P> out, const int* flags) {
-  dslash_m_body<P, NL, N>(a, out, flags);
-}
-
-// FP32 with up to four right-hand sides fits in 80 registers without
-// spilling: six resident blocks (24 warps) hide more latency than the five
-// an uncapped build allows.  (The FP64 and 16-bit kernels would spill.)
-constexpr int MRHS_CAPPED_MINB = 6;
-__host__ __device__ constexpr bool mrhs_capped(int p, int n) { return p == 32 && n <= 4; }
-
-template <int P, int NL, int N>
-__global__ void __launch_bounds__(MB, MRHS_CAPPED_MINB) k_dslash_m_cap(DslashArgsM<P> a, SpinorM<P> out,
-                                                                      const int* flags) {
-  dslash_m_body<P, NL, N>(a, out, flags);
-}
-
-// out_r = ax x_r + ay y_r + ad (D in)_r; RED = 1: Re<x_r, out_r>, RED = 2:
-// ||out_r||^2, one FP64 sum per system, finalised by the last block.
-template <int P, int NL, int N, int RED>
-__device__ __forceinline__ void dslash_m_epi_body(const DslashArgsM<P>& a, SpinorM<Acc<P>::value> out, SpinorM<P> x,
-                                                  double ax, SpinorM<Acc<P>::value> y, double ay, double ad,
-                                                  RedBuf rb, RedTarget tgt, const int* flags) {
-  using A2 = typename Prec<P>::A2;
-  using A = typename Prec<P>::A;
-  constexpr int PA = Acc<P>::value;
-  if (stopped(flags)) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  double red[N];
-#pragma unroll
-  for (int r = 0; r < N; ++r) red[r] = 0.0;
-  if (s < a.g.Vh) {
-    // the epilogue's x_r are read after the stencil: start them towards L2 now
-#pragma unroll
-    for (int r = 0; r < N; ++r) prefetch_spinor_l2<P>(SpinorLoadM<P>::one(x, r), s);
-    A2 d[N][3];
-    dslash_site_m<P, NL, N>(a, s, d);
-    const A cx = (A)ax, cd = (A)ad, cy = (A)ay;
-#pragma unroll
-    for (int r = 0; r < N; ++r) {
-      A2 xv[3], o[3];
-      SpinorLoadM<P>::ld(x, s, r, xv);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        o[i].x = cx * xv[i].x + cd * d[r][i].x;
-        o[i].y = cx * xv[i].y + cd * d[r][i].y;
-      }
-      if (ay != 0.0) {
-        A2 yv[3];
-        SpinorLoadM<PA>::ld(y, s, r, yv);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          o[i].x += cy * yv[i].x;
-          o[i].y += cy * yv[i].y;
-        }
-      }
-      SpinorLoadM<PA>::st(out, s, r, o);
-      if (RED) {
-        Acc1<A> acc;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          acc.add_prod(RED == 1 ? xv[i].x : o[i].x, o[i].x);
-          acc.add_prod(RED == 1 ? xv[i].y : o[i].y, o[i].y);
-        }
-        red[r] = acc.value();
-      }
-    }
-  }
-  if (RED) grid_reduce<N>(red, rb, tgt);
-}
-
-template <int P, int NL, int N, int RED>
-__global__ void __launch_bounds__(MB)
-    k_dslash_m_epi(DslashArgsM<P> a, SpinorM<Acc<P>::value> out, SpinorM<P> x, double ax, SpinorM<Acc<P>::value> y,
-                   double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags) {
-  dslash_m_epi_body<P, NL, N, RED>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
-}
-
-template <int P, int NL, int N, int RED>
-__global__ void __launch_bounds__(MB, MRHS_CAPPED_MINB)
-    k_dslash_m_epi_cap(DslashArgsM<P> a, SpinorM<Acc<P>::value> out, SpinorM<P> x, double ax,
-                       SpinorM<Acc<P>::value> y, double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags) {
-  dslash_m_epi_body<P, NL, N, RED>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
-}
 
 // ------------------------------------------------------------ level 1
 // grid-stride over sites, all N systems of a site per trip
@@ -382,25 +285,42 @@ template <int P, int N> __global__ void k_mnorm2(SpinorM<P> v, RedBuf rb, RedTar
 // Before a group's reliable-update kernels in each round of the loop: is an
 // update due (a flag set by the last chunk)?  ru_skip = 0 lets the update's
 // kernels run, F_CONVERGED makes them return at once.
+// With double-float updates the gate also picks between them and the one
+// FP64 update that moves the anchor (see McgState): ru_skip gates the
+// double-float kernels, ru_skip64 the FP64 ones.
+__device__ inline bool mcg_anchor_due(const McgState* g) {
+  if (!g->use_df || g->anchored) return false;
+  for (int i = 0; i < g->n; ++i)
+    if (((g->active >> i) & 1) && !(g->sys[i].rr < g->anchor_rr[i])) return false;
+  return true;
+}
+
 __global__ void k_mcg_ru_gate(McgState* g) {
-  if (g->done) {
-    g->ru_skip = F_CONVERGED;
-    return;
-  }
+  g->ru_skip = F_CONVERGED;
+  g->ru_skip64 = F_CONVERGED;
+  if (g->done) return;
   if (g->flags & F_BREAKDOWN) {
     g->done = 1;
     g->status = STAG_EBREAKDOWN;
-    g->ru_skip = F_CONVERGED;
     return;
   }
-  g->ru_skip = (g->flags & (F_CONVERGED | F_NEED_RU | F_ITER_CAP)) ? 0 : F_CONVERGED;
+  if (!(g->flags & (F_CONVERGED | F_NEED_RU | F_ITER_CAP))) return;
+  if (mcg_anchor_due(g)) {
+    g->ru_skip64 = 0;
+    g->anchored = 1;
+  } else if (g->use_df) {
+    g->ru_skip = 0;
+  } else {
+    g->ru_skip64 = 0;
+  }
 }
 
 // After them: retire the group (every system at its target, an error, the
 // iteration cap) or let it iterate on from the new direction.
 __global__ void k_mcg_ru_decide(McgState* g) {
-  if (g->ru_skip) return;
+  if (g->ru_skip && g->ru_skip64) return;
   g->ru_skip = F_CONVERGED;
+  g->ru_skip64 = F_CONVERGED;
   if (g->flags & F_BREAKDOWN) {
     g->done = 1;
     g->status = STAG_EBREAKDOWN;

@@ -377,6 +377,15 @@ struct McgState {
   int status;     // STAG_OK or the error that ended the group
   int ru_skip;    // F_CONVERGED while no reliable update is due (a stop word for its kernels), else 0
   int skip_xpay;  // 1: the next direction update must not run (after the start or an update)
+  // double-float reliable updates measure r = r_a - M (y - y_a) from an
+  // anchor (y_a, r_a = b - M y_a); the anchor starts at (0, b) and is moved
+  // once, by an FP64 update, when every active system's iterated ||r||^2
+  // has fallen below anchor_rr[i] (the FP64-class accuracy of the residual
+  // then no longer depends on the size of y)
+  int use_df;     // 1: updates in double-float (ru_skip gates them), FP64 anchor gated by ru_skip64
+  int anchored;   // the anchor has been moved
+  int ru_skip64;  // stop word of the FP64 anchor update (graph-resident loop)
+  double anchor_rr[MAX_RHS];
 };
 
 enum RedOp : int {
@@ -391,6 +400,8 @@ enum RedOp : int {
   RED_MCG_BETA = 8,   // per-system ||r||^2 -> beta, activity, group flags
   RED_MCG_RU_RESID = 9,  // per-system true ||r||^2 after a reliable update
   RED_MCG_RU_ORTHO = 10, // per-system <r,p> (re, im pairs)
+  RED_RU_BOTH = 11,      // true ||r||^2, then <r,p> (re, im): RU_RESID followed by RU_ORTHO
+  RED_MCG_RU_BOTH = 12,  // per-system true ||r||^2 (n values), then <r,p> pairs (2n values)
 };
 
 struct RedTarget {
@@ -421,6 +432,55 @@ __device__ inline void cg_beta_update(CgState* st, double rr_new) {
   if (st->iter >= st->max_iter) st->flags |= F_ITER_CAP;
 }
 
+// Reliable update, single system: the FP64-class true ||r||^2 restarts the
+// recurrence (beta, rr, rr_max) ...
+__device__ inline void fin_ru_resid(CgState* st, double rr) {
+  st->rr_true = rr;
+  if (!finite_d(rr)) {
+    st->flags |= F_BREAKDOWN;
+    return;
+  }
+  st->beta = rr / st->rr_prev;
+  st->rr = rr;
+  st->rr_max = rr;
+  st->reliable_updates += 1;
+  st->flags &= ~(F_CONVERGED | F_NEED_RU);
+}
+// ... and <r,p>/||r||^2 (v = re, im) re-orthogonalises the search direction.
+__device__ inline void fin_ru_ortho(CgState* st, const double* v) {
+  st->ortho_re = st->rr > 0.0 ? v[0] / st->rr : 0.0;
+  st->ortho_im = st->rr > 0.0 ? v[1] / st->rr : 0.0;
+}
+// The same for every system of a group (v: n norms; then n (re, im) pairs).
+__device__ inline void fin_mcg_ru_resid(McgState* g, const double* v) {
+  int active = 0;
+  for (int i = 0; i < g->n; ++i) {
+    CgState* st = &g->sys[i];
+    const double rr = v[i];
+    st->rr_true = rr;
+    if (!finite_d(rr)) {
+      g->flags |= F_BREAKDOWN;
+      continue;
+    }
+    st->beta = st->rr_prev > 0.0 ? rr / st->rr_prev : 0.0;
+    st->rr = rr;
+    st->rr_max = rr;
+    if (rr > st->target) active |= 1 << i;
+  }
+  g->active = active;
+  g->reliable_updates += 1;
+  g->flags &= ~(F_CONVERGED | F_NEED_RU);
+  if (active == 0) g->flags |= F_CONVERGED;
+}
+__device__ inline void fin_mcg_ru_ortho(McgState* g, const double* v) {
+  for (int i = 0; i < g->n; ++i) {
+    CgState* st = &g->sys[i];
+    st->ortho_re = st->rr > 0.0 ? v[2 * i] / st->rr : 0.0;
+    st->ortho_im = st->rr > 0.0 ? v[2 * i + 1] / st->rr : 0.0;
+    if (!((g->active >> i) & 1)) st->beta = 0.0;
+  }
+}
+
 __device__ inline void finalize(const RedTarget& t, const double* v, int nv) {
   switch (t.op) {
     case RED_STORE:
@@ -436,27 +496,16 @@ __device__ inline void finalize(const RedTarget& t, const double* v, int nv) {
     case RED_CG_BETA:
       cg_beta_update((CgState*)t.state, v[0]);
       break;
-    case RED_RU_RESID: {
-      CgState* st = (CgState*)t.state;
-      double rr = v[0];
-      st->rr_true = rr;
-      if (!finite_d(rr)) {
-        st->flags |= F_BREAKDOWN;
-        break;
-      }
-      st->beta = rr / st->rr_prev;
-      st->rr = rr;
-      st->rr_max = rr;
-      st->reliable_updates += 1;
-      st->flags &= ~(F_CONVERGED | F_NEED_RU);
+    case RED_RU_RESID:
+      fin_ru_resid((CgState*)t.state, v[0]);
       break;
-    }
-    case RED_RU_ORTHO: {
-      CgState* st = (CgState*)t.state;
-      st->ortho_re = st->rr > 0.0 ? v[0] / st->rr : 0.0;
-      st->ortho_im = st->rr > 0.0 ? v[1] / st->rr : 0.0;
+    case RED_RU_ORTHO:
+      fin_ru_ortho((CgState*)t.state, v);
       break;
-    }
+    case RED_RU_BOTH:
+      fin_ru_resid((CgState*)t.state, v[0]);
+      fin_ru_ortho((CgState*)t.state, v + 1);
+      break;
     case RED_MS_ALPHA: {
       MsState* ms = (MsState*)t.state;
       CgState* st = &ms->cg;
@@ -565,36 +614,16 @@ __device__ inline void finalize(const RedTarget& t, const double* v, int nv) {
       if (g->iter >= g->max_iter) g->flags |= F_ITER_CAP;
       break;
     }
-    case RED_MCG_RU_RESID: {
-      McgState* g = (McgState*)t.state;
-      int active = 0;
-      for (int i = 0; i < g->n; ++i) {
-        CgState* st = &g->sys[i];
-        const double rr = v[i];
-        st->rr_true = rr;
-        if (!finite_d(rr)) {
-          g->flags |= F_BREAKDOWN;
-          continue;
-        }
-        st->beta = st->rr_prev > 0.0 ? rr / st->rr_prev : 0.0;
-        st->rr = rr;
-        st->rr_max = rr;
-        if (rr > st->target) active |= 1 << i;
-      }
-      g->active = active;
-      g->reliable_updates += 1;
-      g->flags &= ~(F_CONVERGED | F_NEED_RU);
-      if (active == 0) g->flags |= F_CONVERGED;
+    case RED_MCG_RU_RESID:
+      fin_mcg_ru_resid((McgState*)t.state, v);
       break;
-    }
-    case RED_MCG_RU_ORTHO: {
+    case RED_MCG_RU_ORTHO:
+      fin_mcg_ru_ortho((McgState*)t.state, v);
+      break;
+    case RED_MCG_RU_BOTH: {
       McgState* g = (McgState*)t.state;
-      for (int i = 0; i < g->n; ++i) {
-        CgState* st = &g->sys[i];
-        st->ortho_re = st->rr > 0.0 ? v[2 * i] / st->rr : 0.0;
-        st->ortho_im = st->rr > 0.0 ? v[2 * i + 1] / st->rr : 0.0;
-        if (!((g->active >> i) & 1)) st->beta = 0.0;
-      }
+      fin_mcg_ru_resid(g, v);
+      fin_mcg_ru_ortho(g, v + g->n);
       break;
     }
   }

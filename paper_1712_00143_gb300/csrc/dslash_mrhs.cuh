@@ -41,6 +41,20 @@ template <int P> struct SpinorLoadM {
   }
 };
 
+// The N-right-hand-side operator halves (mrhs_kernels.cuh; instantiated in
+// mrhs64.cu, mrhs32.cu, mrhs16.cu, mrhs15.cu): out = D in on parity
+// out_parity, and out = ax x + ay y + ad D in with an optional per-system
+// reduction (RED 1: Re<x, out>, 2: ||out||^2), in the launch variant the
+// autotuner chose for (P, N) on this lattice (tune_mrhs).
+template <int P, int N>
+int mdslash(const stag_lattice_s* lat, SpinorM<P> out, SpinorM<P> in, int out_parity, const int* flags,
+            cudaStream_t st);
+template <int P, int N, int RED>
+int mdslash_epi(const stag_lattice_s* lat, SpinorM<Acc<P>::value> out, SpinorM<P> in, int out_parity, SpinorM<P> x,
+                double ax, SpinorM<Acc<P>::value> y, double ay, double ad, RedScratch rs, RedTarget tgt,
+                const int* flags, cudaStream_t st);
+template <int P, int N> int tune_mrhs(stag_lattice_s* lat, cudaStream_t st);
+
 template <int P> struct DslashArgsM {
   Geom g;
   int out_parity;

@@ -8,6 +8,7 @@
 
 #include "../../include/stag.h"
 #include "common.cuh"
+#include "df.cuh"
 
 namespace stag {
 
@@ -46,7 +47,14 @@ struct stag_lattice_s {
   stag::Geom g;
   int dims[4];
   double c3 = -1.0 / 24.0;
-  stag::LinkCopy links[4];  // by stag_prec
+  int autotune = 1;  // time launch variants on this lattice (stag_link_opts.autotune)
+  // launch variant of the N-right-hand-side kernels per (format, N = 2, 4, 8)
+  // (-1: not chosen yet) and its time per operator application (us)
+  struct MrhsTune {
+    int variant = -1;
+    float us = 0.f;
+  } mrhs[5][4];
+  stag::LinkCopy links[5];  // by stag_prec (STAG_DF64 = 4: FP64 split into hi + lo floats)
   stag::Workspace ws;
 };
 
@@ -56,6 +64,10 @@ namespace stag {
 void prof_begin(const char* family, cudaStream_t s);
 void prof_end(cudaStream_t s);
 void prof_flush_completed();
+// Sequence mark of the next profiling record, and the discard of the records
+// made since a mark (a chunk of iterations cut short by a stop flag).
+long long prof_mark();
+void prof_discard_since(long long mark);
 void count_launch();
 // While capturing a CUDA graph: no profiling events, and kernel launches are
 // counted aside; set_capturing(false) returns how many were captured.
@@ -86,6 +98,15 @@ int get_red_scratch(stag_lattice_s* lat, const char* name, RedScratch* out, int 
 
 // A Spinor<P> living in the handle's workspace buffer `name`.
 template <int P> Spinor<P> ws_spinor(stag_lattice_s* lat, const std::string& name, int* status);
+
+// ------------------------------------------------------------------- autotuner cache (tune.cu)
+// Key of a tuned launch: kernel family, storage format, Naik entries per
+// hop, right-hand sides, lattice extents.
+std::string tune_key(const char* kernel, int prec, int nl, int nrhs, const int dims[4]);
+// Process-wide cache of tuned variants (loaded on first use from the JSON
+// file named by STAG_TUNE_CACHE, if set; rewritten there on every put).
+bool tune_cache_get(const std::string& key, int* variant, double* us);
+void tune_cache_put(const std::string& key, int variant, double us);
 
 // ------------------------------------------------------------------- links
 int build_link_copy(stag_lattice_s* lat, int prec, int recon, const double2* fat, const double2* lng,
@@ -149,5 +170,40 @@ int launch_ms_r_update(Spinor<Acc<P>::value> r, Spinor<Acc<P>::value> Ap, MsStat
 template <int P>
 int launch_ms_shift_update(Spinor<Acc<P>::value>* xs, Spinor<P>* ps, int nshift, int base, Spinor<Acc<P>::value> r,
                            MsState* state, int expect_iter, cudaStream_t st);
+
+
+// ------------------------------------------------------------------- double-float (dslash_df.cu)
+// t = D in on parity out_parity for n systems of DF fields ([n][Vh][3] float4),
+// with the handle's DF link copy; up to four systems per launch.
+int launch_dslash_df(const stag_lattice_s* lat, DfField out, DfField in, int n, int out_parity, const int* stop,
+                     cudaStream_t st);
+// out_r = ad (D in)_r + ax x_r + ay y_r (ad = +1 or -1; x, y DF fields or null)
+int launch_dslash_df_epi(const stag_lattice_s* lat, DfField out, DfField in, int n, int out_parity, DfField x,
+                         double ax, DfField y, double ay, double ad, const int* stop, cudaStream_t st);
+// times the double-float hop kernel's launch variants on this lattice
+int tune_df(stag_lattice_s* lat, cudaStream_t st);
+// FP64 [n][Vh][3] <-> DF
+int launch_df_from_double(DfField out, const double2* in, int n, cudaStream_t st);
+int launch_df_to_double(double2* out, DfField in, int n, cudaStream_t st);
+// y_r += xh_r (FP64), xh_r = 0, ydf_r = split(y_r - ya_r) (ya: the anchor,
+// null = 0); n in {1, 2, 4, 8}; MRHS layouts
+template <int PV>
+int launch_accumulate_df(void* y64, void* xh, DfField ydf, const void* ya, int n, const int* stop, cudaStream_t st);
+// the anchor moves to (y, r): ya = y, ra = split(r) (FP64 fields, n systems)
+int launch_df_anchor(void* ya, DfField ra, const void* y, const void* r, int n, const int* stop, cudaStream_t st);
+// Reliable updates in double-float are measured from an anchor (y_a, r_a =
+// b - M y_a), which starts at (0, b) and is moved once, by an FP64 update,
+// when the iterated residual has fallen below this fraction of ||b|| (squared):
+// from then on the update's rounding error is relative to y - y_a, not to y.
+constexpr double kDfAnchorRel2 = 1e-10;
+// rh_r = r_r (rounded), ||rh_r||^2 and <rh_r, p_r> -> tgt (RED_RU_BOTH for one
+// system, RED_MCG_RU_BOTH for a group)
+template <int P>
+int launch_ru_convert_dot_df(void* rh, DfField r, const void* p, int n, RedScratch rs, RedTarget tgt, const int* stop,
+                             cudaStream_t st);
+// ||v_r||^2 -> tgt (n values)
+int launch_norm2_df(DfField v, int n, RedScratch rs, RedTarget tgt, cudaStream_t st);
+// Krylov-loop (PV) fields from DF fields
+template <int PV> int launch_convert_from_df(void* out, DfField in, int n, cudaStream_t st);
 
 }  // namespace stag

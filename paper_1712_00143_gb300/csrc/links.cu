@@ -1,7 +1,8 @@
 // links.cu -- gauge-field remap: canonical [V][4][3][3] complex double links
-// (no phases) -> the internal per-parity hop layout in FP64, FP32, FP16 or
-// 16-bit fixed point, with the staggered phase eta_mu(x), the 1/2 and the
-// sign of the backward hops folded in.  The paper notes that remapping from
+// (no phases) -> the internal per-parity hop layout in FP64, double-float
+// (FP64 as hi + lo floats), FP32, FP16 or 16-bit fixed point, with the
+// staggered phase eta_mu(x), the 1/2 and the sign of the backward hops
+// folded in.  The paper notes that remapping from
 // the host code's layout to the library's costs about as much as one call of
 // the routine and keeps it out of its timings (Sec. 4.2; caption of Fig. 9);
 // here it runs once per gauge field, on the GPU.
@@ -24,6 +25,12 @@ __device__ __forceinline__ void store_c(float2* p, double re, double im) {
 }
 __device__ __forceinline__ void store_c(__half2* p, double re, double im) {
   *p = __halves2half2(__double2half(re), __double2half(im));
+}
+// double-float: {hi.re, hi.im, lo.re, lo.im}, hi the nearest float, lo the
+// nearest float to the remainder (about 48 significant bits in all)
+__device__ __forceinline__ void store_c(float4* p, double re, double im) {
+  const float hre = (float)re, him = (float)im;
+  *p = make_float4(hre, him, (float)(re - (double)hre), (float)(im - (double)him));
 }
 __device__ __forceinline__ void store_c(short2* p, double re, double im) {
   // re, im are normalised to [-1, 1]
@@ -157,8 +164,8 @@ int build_link_copy(stag_lattice_s* lat, int prec, int recon, const double2* fat
                     cudaStream_t st) {
   const Geom& g = lat->g;
   LinkCopy& L = lat->links[prec];
-  int nl = (prec == STAG_FP64 || recon != 12) ? 9 : 6;
-  size_t eb = prec == STAG_FP64 ? 16 : prec == STAG_FP32 ? 8 : 4;
+  int nl = (prec == STAG_FP64 || prec == STAG_DF64 || recon != 12) ? 9 : 6;
+  size_t eb = (prec == STAG_FP64 || prec == STAG_DF64) ? 16 : prec == STAG_FP32 ? 8 : 4;
   size_t bytes = (size_t)2 * 4 * (18 + 2 * nl) * g.Vh * eb;
   if (L.data) cudaFree(L.data);
   L = LinkCopy();
@@ -191,6 +198,7 @@ int build_link_copy(stag_lattice_s* lat, int prec, int recon, const double2* fat
   double ic3 = 1.0 / lat->c3;
   switch (prec) {
     case STAG_FP64: status = run_load<double2, 1, 9>(fat, lng, g, L.data, ifs, ils, ic3, err, st); break;
+    case STAG_DF64: status = run_load<float4, 1, 9>(fat, lng, g, L.data, ifs, ils, ic3, err, st); break;
     case STAG_FP32:
       status = nl == 9 ? run_load<float2, 2, 9>(fat, lng, g, L.data, ifs, ils, ic3, err, st)
                        : run_load<float2, 2, 6>(fat, lng, g, L.data, ifs, ils, ic3, err, st);

@@ -1,0 +1,24 @@
+// mrhs32.cu -- instantiation of the N-right-hand-side Dslash kernels, their
+// launch variants and the autotuner for storage format 32 (see mrhs_kernels.cuh).
+#include "mrhs_kernels.cuh"
+
+namespace stag {
+STAG_INSTANTIATE_MRHS_N(32, 2)
+STAG_INSTANTIATE_MRHS_N(32, 4)
+STAG_INSTANTIATE_MRHS_N(32, 8)
+}  // namespace stag
+
+using namespace stag;
+
+extern "C" int stag_tuned_mrhs(stag_lattice_t lat, int prec, int nrhs, int* threads_per_site, int* min_blocks,
+                               double* us) {
+  if (!lat || prec < 0 || prec > 3 || !lat->links[prec].present) return STAG_EINVAL;
+  if (nrhs != 2 && nrhs != 4 && nrhs != 8) return STAG_EINVAL;
+  const auto& slot = lat->mrhs[prec][mrhs_nindex(nrhs)];
+  const int p = prec == STAG_FP64 ? 64 : prec == STAG_FP32 ? 32 : prec == STAG_FP16 ? 16 : 15;
+  const int v = slot.variant >= 0 ? slot.variant : mrhs_default_variant(p, nrhs);
+  if (threads_per_site) *threads_per_site = mvariant(v).sp;
+  if (min_blocks) *min_blocks = mvariant(v).minb;
+  if (us) *us = slot.variant >= 0 ? slot.us : 0.0;
+  return STAG_OK;
+}

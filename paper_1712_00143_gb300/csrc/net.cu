@@ -7,6 +7,7 @@
 #include <cstring>
 #include <vector>
 
+#include "flags.h"
 #include "net_tc.cuh"
 
 struct stag_net_s {
@@ -270,12 +271,18 @@ static void launch_layer(const NetRun& R, int l, const float2* in, float2* pre, 
 // STAG_ETIMEOUT if a tensor-core layer gave up a bounded wait since the
 // last check (the flag is cleared here).  Synchronous.
 static int net_tc_status() {
-  int v = 0;
-  if (cudaMemcpyFromSymbol(&v, tc::g_tc_error, sizeof(int)) != cudaSuccess) return STAG_ECUDA;
-  if (!v) return STAG_OK;
-  v = 0;
-  cudaMemcpyToSymbol(tc::g_tc_error, &v, sizeof(int));
-  return STAG_ETIMEOUT;
+  auto read = [](int* v) {
+    const cudaError_t e = cudaMemcpyFromSymbol(v, tc::g_tc_error, sizeof(int));
+    if (e != cudaSuccess) cudaGetLastError();
+    return e == cudaSuccess ? 0 : 1;
+  };
+  auto clear = []() {
+    const int z = 0;
+    const cudaError_t e = cudaMemcpyToSymbol(tc::g_tc_error, &z, sizeof(int));
+    if (e != cudaSuccess) cudaGetLastError();
+    return e == cudaSuccess ? 0 : 1;
+  };
+  return take_flag(read, clear, STAG_ETIMEOUT);
 }
 
 // Layer l forward (ch[l] -> ch[l+1]); supported widths 1 and 16.

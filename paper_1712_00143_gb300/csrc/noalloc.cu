@@ -50,6 +50,10 @@ extern "C" int stag_apply_m_noalloc(stag_lattice_t lat, void* out, const void* i
   if (!lat || !out || !in) return STAG_EINVAL;
   if (!lat->links[STAG_FP64].present) return STAG_EINVAL;
   if (lat->g.Vh > STAG_NOALLOC_MAX_VH) return STAG_EINVAL;
+  // in is read through the read-only path by the kernel that writes out
+  const size_t bytes = (size_t)lat->g.Vh * 48;
+  const char *pi = (const char*)in, *po = (const char*)out;
+  if (pi < po + bytes && po < pi + bytes) return STAG_EINVAL;
   void* scratch = nullptr;
   int s = noalloc_scratch(&scratch);
   if (s) return s;
@@ -63,13 +67,18 @@ extern "C" int stag_apply_m_noalloc(stag_lattice_t lat, void* out, const void* i
   const int B = 256, G = (Vh + B - 1) / B;
   // t = D_oe in (odd sites): every entry of t is written before it is read
   DslashArgs<64> a1 = make_args<64>(lat, x, 1);
-  count_launch();
-  k_dslash<64, 9, 256, 1><<<G, B, 0, st>>>(a1, t, nullptr);
+  {
+    ProfScope ps("dslash64", st);
+    k_dslash<64, 9, 256, 1><<<G, B, 0, st>>>(a1, t, nullptr);
+  }
   if ((s = last_launch_status())) return s;
   // out = (m^2 + shift) in - D_eo t (even sites)
   DslashArgs<64> a2 = make_args<64>(lat, t, 0);
-  count_launch();
-  k_dslash_epi<64, 9, 0, 256, 1><<<G, B, 0, st>>>(a2, o, x, mass * mass + shift, none, 0.0, -1.0, RedBuf{nullptr, nullptr},
-                                          RedTarget{RED_STORE, nullptr, nullptr}, nullptr);
+  {
+    ProfScope ps("dslash64_epi", st);
+    k_dslash_epi<64, 9, 0, 256, 1><<<G, B, 0, st>>>(a2, o, x, mass * mass + shift, none, 0.0, -1.0,
+                                                    RedBuf{nullptr, nullptr}, RedTarget{RED_STORE, nullptr, nullptr},
+                                                    nullptr);
+  }
   return last_launch_status();
 }

@@ -79,9 +79,25 @@ static int cg_solve(stag_lattice_s* lat, double2* x_can, const double2* b_can, d
   Spinor<PV> rh = ws_spinor<PV>(lat, "cg.rh", &s);
   CgState* dst = (CgState*)lat->ws.get("cg.state", sizeof(CgState), &s);
   double* dscal = (double*)lat->ws.get("cg.scalars", 64, &s);
+  // reliable updates in double-float when the handle holds that link copy,
+  // measured from an anchor (ya64, its residual radf): r = r_a - M (y - y_a)
+  const bool use_df = P != 64 && lat->links[STAG_DF64].present;
+  DfField radf{nullptr, Vh}, ydf{nullptr, Vh}, tdf{nullptr, Vh}, rdf{nullptr, Vh};
+  Spinor<64> ya64{nullptr, Vh};
+  if (use_df) {
+    ya64 = ws_spinor<64>(lat, "cg.ya", &s);
+    radf.v = (float4*)lat->ws.get("cg.radf", df_bytes(Vh), &s);
+    ydf.v = (float4*)lat->ws.get("cg.ydf", df_bytes(Vh), &s);
+    tdf.v = (float4*)lat->ws.get("cg.tdf", df_bytes(Vh), &s);
+    rdf.v = (float4*)lat->ws.get("cg.rdf", df_bytes(Vh), &s);
+  }
   if (s) return s;
   RedScratch rs;
-  TRY(get_red_scratch(lat, "cg", &rs));
+  TRY(get_red_scratch(lat, "cg", &rs, 3));
+  auto true_residual_df = [&]() -> int {
+    TRY(launch_dslash_df(lat, tdf, ydf, 1, 1, nullptr, st));
+    return launch_dslash_df_epi(lat, rdf, tdf, 1, 0, ydf, -shift, radf, 1.0, 1.0, nullptr, st);
+  };
   PinnedState pin(sizeof(CgState) + 64);
   if (!pin.h) return STAG_ENOMEM;
   CgState* hs = (CgState*)pin.h;
@@ -90,9 +106,21 @@ static int cg_solve(stag_lattice_s* lat, double2* x_can, const double2* b_can, d
   // ||b||^2 and the initial residual
   TRY(launch_from_canonical<64>(b64, b_can, Vh, st));
   TRY(launch_norm2<64>(b64, rs, RedTarget{RED_STORE, nullptr, dscal}, st));
+  if (use_df) {
+    // the anchor starts at (0, b)
+    TRY(launch_df_from_double(radf, (const double2*)b64.v, 1, st));
+    TRY(launch_zero(ya64.v, spinor_bytes<64>(Vh), st));
+  }
+  bool anchored = false;
   if (prm.use_initial_guess) {
     TRY(launch_from_canonical<64>(y64, x_can, Vh, st));
-    TRY(true_residual(lat, r64, b64, y64, t64, shift, rs, RedTarget{RED_STORE, nullptr, dscal + 1}, st));
+    if (use_df) {
+      TRY(launch_df_from_double(ydf, (const double2*)y64.v, 1, st));
+      TRY(true_residual_df());
+      TRY(launch_norm2_df(rdf, 1, rs, RedTarget{RED_STORE, nullptr, dscal + 1}, st));
+    } else {
+      TRY(true_residual(lat, r64, b64, y64, t64, shift, rs, RedTarget{RED_STORE, nullptr, dscal + 1}, st));
+    }
   } else {
     TRY(launch_zero(y64.v, spinor_bytes<64>(Vh), st));
     TRY(cuda_status(cudaMemcpyAsync(r64.v, b64.v, spinor_bytes<64>(Vh), cudaMemcpyDeviceToDevice, st)));
@@ -135,7 +163,10 @@ static int cg_solve(stag_lattice_s* lat, double2* x_can, const double2* b_can, d
   if (rr0 > target && prm.max_iter > 0) {
     TRY(cuda_status(cudaMemcpyAsync(dst, hs, sizeof(CgState), cudaMemcpyHostToDevice, st)));
     // sloppy copies: rh = r, xh = 0, p = rh
-    TRY(launch_convert<PV, 64>(rh, r64, st));
+    if (use_df && prm.use_initial_guess)
+      TRY(launch_convert_from_df<PV>(rh.v, rdf, 1, st));
+    else
+      TRY(launch_convert<PV, 64>(rh, r64, st));
     TRY(launch_zero(xh.v, spinor_bytes<PV>(Vh), st));
     TRY(launch_convert<P, PV>(p, rh, st));
     const int* flags = &dst->flags;
@@ -149,6 +180,7 @@ static int cg_solve(stag_lattice_s* lat, double2* x_can, const double2* b_can, d
         status = STAG_ENOTCONV;
         break;
       }
+      const long long mark = prof_mark();
       for (int i = 0; i < C; ++i) {
         if (pending_p) TRY(launch_cg_xpay<P>(p, rh, dst, st));
         TRY(launch_dslash<P>(lat, t, p, 1, flags, st));
@@ -159,21 +191,45 @@ static int cg_solve(stag_lattice_s* lat, double2* x_can, const double2* b_can, d
       }
       TRY(cuda_status(cudaMemcpyAsync(hs, dst, sizeof(CgState), cudaMemcpyDeviceToHost, st)));
       TRY(cuda_status(cudaStreamSynchronize(st)));
+      if (hs->flags & F_STOP) prof_discard_since(mark);  // launches after the flag returned at once
       prof_flush_completed();
       if (hs->flags & F_BREAKDOWN) {
         status = STAG_EBREAKDOWN;
         break;
       }
       if (hs->flags & (F_CONVERGED | F_NEED_RU | F_ITER_CAP)) {
-        // reliable update: y += xh, r = b - M y in FP64, rh = r, and the
-        // search direction re-orthogonalised against the new residual
-        TRY(launch_accumulate<PV>(y64, xh, st));
-        TRY(true_residual(lat, r64, b64, y64, t64, shift, rs, RedTarget{RED_RU_RESID, dst, nullptr}, st));
-        TRY(launch_ru_convert_dot<P>(rh, r64, p, dst, rs, st));
-        TRY(launch_ru_p<P>(p, rh, dst, st));
+        // reliable update: y += xh, r = b - M y (FP64-class), rh = r, and
+        // the search direction re-orthogonalised against the new residual
+        auto update = [&](bool df) -> int {
+          if constexpr (P != 64) {
+            if (df) {
+              TRY(launch_accumulate_df<PV>(y64.v, xh.v, ydf, ya64.v, 1, nullptr, st));
+              TRY(true_residual_df());
+              TRY(launch_ru_convert_dot_df<P>(rh.v, rdf, p.v, 1, rs, RedTarget{RED_RU_BOTH, dst, nullptr}, nullptr,
+                                              st));
+            }
+          }
+          if (!df) {
+            TRY(launch_accumulate<PV>(y64, xh, st));
+            TRY(true_residual(lat, r64, b64, y64, t64, shift, rs, RedTarget{RED_RU_RESID, dst, nullptr}, st));
+            TRY(launch_ru_convert_dot<P>(rh, r64, p, dst, rs, st));
+          }
+          TRY(launch_ru_p<P>(p, rh, dst, st));
+          if (!df && use_df) {
+            // an FP64 update moves the anchor of the double-float ones
+            TRY(launch_df_anchor(ya64.v, radf, y64.v, r64.v, 1, nullptr, st));
+            anchored = true;
+          }
+          TRY(cuda_status(cudaMemcpyAsync(hs, dst, sizeof(CgState), cudaMemcpyDeviceToHost, st)));
+          return cuda_status(cudaStreamSynchronize(st));
+        };
+        // double-float, except the one FP64 update that moves the anchor once
+        // the iterated residual is small
+        TRY(update(use_df && (anchored || !(hs->rr < kDfAnchorRel2 * bb))));
         pending_p = false;
-        TRY(cuda_status(cudaMemcpyAsync(hs, dst, sizeof(CgState), cudaMemcpyDeviceToHost, st)));
-        TRY(cuda_status(cudaStreamSynchronize(st)));
+        // a double-float residual at the target is judged once more in FP64
+        // (one FP64 operator pair per solve): the final verdict is FP64's
+        if (use_df && !(hs->flags & F_BREAKDOWN) && hs->rr_true <= target) TRY(update(false));
         if (hs->flags & F_BREAKDOWN) {
           status = STAG_EBREAKDOWN;
           break;
@@ -286,6 +342,7 @@ static int ms_solve(stag_lattice_s* lat, double2* const* x_can, const double2* b
       status = STAG_ENOTCONV;
       break;
     }
+    const long long mark = prof_mark();
     for (int i = 0; i < C; ++i) {
       TRY(launch_dslash<P>(lat, t, ps[base], 1, flags, st));
       TRY(launch_dslash_epi<P>(lat, Ap, t, 0, ps[base], shift0, none_spinor<PV>(Vh), 0.0, -1.0, 1, rs,
@@ -295,6 +352,7 @@ static int ms_solve(stag_lattice_s* lat, double2* const* x_can, const double2* b
     }
     TRY(cuda_status(cudaMemcpyAsync(hs, dst, sizeof(MsState), cudaMemcpyDeviceToHost, st)));
     TRY(cuda_status(cudaStreamSynchronize(st)));
+    if (hs->cg.flags & F_STOP) prof_discard_since(mark);
     prof_flush_completed();
     iter0 = hs->cg.iter;
     if (hs->cg.flags & F_BREAKDOWN) {

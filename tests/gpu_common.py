@@ -12,6 +12,9 @@ requires_gpu = pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a
 # (binary16 and fixed point share the 16-bit budget; fixed point, with 15
 # fraction bits, is held to a tighter 5e-4 as well in the tests)
 TOL_DSLASH = {"fp64": 1e-13, "fp32": 1e-6, "fp16": 5e-3, "fx16": 5e-3}
+# double-float (FP64 data, FP32-pipe arithmetic with error-free transformations,
+# about 48 significant bits) is held to the FP64 bound
+TOL_DSLASH_DF = 1e-13
 
 
 def rel_l2(a, b):
@@ -45,3 +48,22 @@ class Field:
         import paper_1712_00143_gb300 as stag
 
         return stag.stag_load_links(self.dims, self.fat_d, self.lng_d, recon_long=recon, prec_mask=prec_mask)
+
+
+def oracle_true_residual(fat, lng, x, b, mass, dims, shift=0.0, chunk=1 << 21):
+    """||b - (M + shift) x|| / ||b|| over the whole field with the oracle's
+    operator, evaluated on chunks of output sites to bound host memory at
+    48^3 x 96 (the same sums as oracle.true_residual)."""
+    import oracle
+
+    Vh = x.shape[0]
+    t = np.empty_like(x)
+    for s0 in range(0, Vh, chunk):
+        idx = np.arange(s0, min(Vh, s0 + chunk))
+        t[idx] = oracle.dslash(fat, lng, x, dims, 1, out_sites=idx)
+    rr = 0.0
+    for s0 in range(0, Vh, chunk):
+        idx = np.arange(s0, min(Vh, s0 + chunk))
+        mx = (mass * mass + shift) * x[idx] - oracle.dslash(fat, lng, t, dims, 0, out_sites=idx)
+        rr += float(np.linalg.norm((b[idx] - mx).ravel()) ** 2)
+    return float(np.sqrt(rr) / np.linalg.norm(b.ravel()))

@@ -47,14 +47,10 @@ def _flat_grads(grads):
     return np.concatenate(parts)
 
 
-@pytest.fixture(scope="module")
-def small():
-    stag = _stag()
-    dims = (4, 4, 4, 6)
-    fat, lng, thin = synth.gauge_field(dims, 0.3, 1020, return_thin=True)
-    h = stag.stag_load_links(dims, dev(fat), dev(lng), recon_long=12)
-    net = stag.stag_net_create(CH, seed=3)
-    # move the biases off zero so the gate's gradient is exercised
+def _net_with_biases(stag, seed=3):
+    """A fresh network with its gate biases moved off zero, so that the
+    gate's gradient is exercised."""
+    net = stag.stag_net_create(CH, seed=seed)
     p = stag.stag_net_get_params(net)
     rng = np.random.default_rng(0)
     off = 0
@@ -64,6 +60,18 @@ def small():
             p[off : off + CH[l + 1]] = rng.normal(0.0, 0.5, CH[l + 1])
             off += CH[l + 1]
     stag.stag_net_set_params(net, p)
+    return net
+
+
+# 4^3 x 6: 192 sites per parity, three whole 64-site tensor-core tiles;
+# 6^4: 648 sites per parity, ten tiles and a ragged one of 8 sites
+@pytest.fixture(scope="module", params=[(4, 4, 4, 6), (6, 6, 6, 6)], ids=["4x4x4x6", "6x6x6x6"])
+def small(request):
+    stag = _stag()
+    dims = request.param
+    fat, lng, thin = synth.gauge_field(dims, 0.3, 1020, return_thin=True)
+    h = stag.stag_load_links(dims, dev(fat), dev(lng), recon_long=12)
+    net = _net_with_biases(stag)
     yield dims, fat, lng, thin, h, net
     net.free()
     h.free()
@@ -91,6 +99,29 @@ def test_forward_matches_oracle(small):
     err = rel_l2(z.cpu().numpy(), zo)
     print(f"network forward rel. L2 error vs FP64 oracle: {err:.2e}")
     assert err < 5e-5
+
+
+def test_forward_32_4_sampled_sites():
+    """The full-size forward (32^4, 1-16-16-16-1, 8192 tensor-core tiles):
+    the oracle evaluates the network on sampled output sites only, layer by
+    layer on their four-hop neighbourhoods (oracle.network.forward_at_sites)."""
+    stag = _stag()
+    dims = (32, 32, 32, 32)
+    f = Field.get(dims)
+    h = f.handle(recon=12, prec_mask=1 << stag.STAG_FP32)
+    net = _net_with_biases(stag)
+    r = synth.random_spinor(dims, 55)
+    z = torch.empty((h.Vh, 3), dtype=torch.complex128, device="cuda")
+    stag.stag_net_apply(net, h, z, dev(r))
+    params = _oracle_params(stag.stag_net_get_params(net, rounded=True), CH)
+    rng = np.random.default_rng(12)
+    sites = np.unique(np.concatenate([rng.integers(0, h.Vh, 300), [0, 63, 64, h.Vh - 1]]))
+    zo = onet.forward_at_sites(f.fat, params, r, dims, oracle.parity_sites(dims, 0), sites)
+    err = rel_l2(z.cpu().numpy()[sites], zo)
+    print(f"32^4 network forward on {len(sites)} sampled sites: rel. L2 error {err:.2e}")
+    assert err < 5e-5
+    net.free()
+    h.free()
 
 
 @pytest.mark.parametrize("kind", ["error", "residual"])

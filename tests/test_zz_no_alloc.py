@@ -1,9 +1,11 @@
 """stag_apply_m_noalloc, the operator entry point that allocates no device
 memory (for callers whose device memory belongs to their own allocator, or
 whose post-start-up code may not allocate).  Its result must match the
-allocating stag_apply_m in FP64, call after call, although every call reuses
-the same static scratch array.  Collected last on purpose: it runs after
-every other test in a full run, and also passes alone in a fresh process."""
+allocating stag_apply_m and the FP64 oracle, call after call, although every
+call reuses the same static scratch array; the device's free memory must not
+change across its calls; overlapping input and output are refused.
+Collected last on purpose: it runs after every other test in a full run, and
+also passes alone in a fresh process."""
 
 import ctypes
 
@@ -11,6 +13,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from gpu_common import TOL_DSLASH, Field, dev, rel_l2, requires_gpu
 
@@ -50,8 +53,46 @@ def test_noalloc_matches_allocating_apply_twice(dims):
         got = torch.full_like(v, complex(np.nan, np.nan))
         _call_noalloc(stag, h, got, v, mass, shift)
         torch.cuda.synchronize()
-        err = rel_l2(got.cpu().numpy(), ref.cpu().numpy())
+        got_h = got.cpu().numpy()
+        err = rel_l2(got_h, ref.cpu().numpy())
         assert err < TOL_DSLASH["fp64"], (dims, call, err)
+        err_o = rel_l2(got_h, oracle.apply_m(f.fat, f.lng, synth.random_spinor(dims, seed), mass, dims, shift=shift))
+        assert err_o < TOL_DSLASH["fp64"], (dims, call, err_o)
+    h.free()
+
+
+def test_noalloc_leaves_device_memory_unchanged():
+    """The defining property: after a first call (which looks up the scratch
+    array's address), further calls change the device's free memory by
+    nothing at all."""
+    stag = _stag()
+    dims = (8, 8, 8, 8)
+    f = Field.get(dims)
+    h = f.handle(prec_mask=1 << stag.STAG_FP64)
+    v = dev(synth.random_spinor(dims, 63))
+    out = torch.empty_like(v)
+    _call_noalloc(stag, h, out, v, 0.1, 0.0)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        _call_noalloc(stag, h, out, v, 0.1, 0.0)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    h.free()
+
+
+def test_noalloc_refuses_overlapping_input_and_output():
+    stag = _stag()
+    dims = (8, 8, 8, 8)
+    f = Field.get(dims)
+    h = f.handle(prec_mask=1 << stag.STAG_FP64)
+    buf = torch.zeros((h.Vh + 1, 3), dtype=torch.complex128, device="cuda")
+    for out in (buf[: h.Vh], buf[1:]):
+        st = stag._lib.stag_apply_m_noalloc(
+            h.ptr, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(buf.data_ptr()), 0.1, 0.0, None
+        )
+        assert st == stag.STAG_EINVAL
     h.free()
 
 
