@@ -47,12 +47,12 @@ FLOP_PER_SITE = 1146
 # algorithmic bytes per output site of one Dslash: 16 link matrices (8 fat x
 # 9 complex + 8 Naik x NL complex) read once, the input vector read once,
 # the output written once
-ELEM_BYTES = {"fp64": 16, "fp32": 8, "fp16": 4, "fx16": 4, "df64": 16}
-VEC_BYTES = {"fp64": 48, "fp32": 24, "fp16": 16, "fx16": 16, "df64": 48}
-MODE_PREC = {"plain64": "fp64", "mixed32": "fp32", "mixed16": "fp16", "mixedfx16": "fx16"}
+ELEM_BYTES = {"fp64": 16, "fp32": 8, "fp16": 4, "fx16": 4, "df64": 16, "fx16l": 4}
+VEC_BYTES = {"fp64": 48, "fp32": 24, "fp16": 16, "fx16": 16, "df64": 48, "fx16l": 24}
+MODE_PREC = {"plain64": "fp64", "mixed32": "fp32", "mixed16": "fp16", "mixedfx16": "fx16", "mixed16l": "fx16l"}
 # arithmetic type of the Krylov loop of each solver mode (FP32 arithmetic on
 # 16-bit storage for the 16-bit modes)
-DTYPE = {"plain64": "f64", "mixed32": "f32", "mixed16": "f32", "mixedfx16": "f32"}
+DTYPE = {"plain64": "f64", "mixed32": "f32", "mixed16": "f32", "mixedfx16": "f32", "mixed16l": "f32"}
 
 
 # the library's kernel families (stag.h, instrumentation)
@@ -69,7 +69,7 @@ def kernel_source_hash(kernel_id="k_dslash"):
     h = hashlib.sha256()
     files = ("dslash_impl.cuh", "common.cuh", "links.cu")
     if kernel_id.startswith("k_dslash_m"):
-        files = files + ("batch_kernels.cuh", "dslash_mrhs.cuh")
+        files = files + ("mrhs_kernels.cuh", "dslash_mrhs.cuh")
     for f in files:
         with open(os.path.join(ROOT, "paper_1712_00143_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
@@ -238,6 +238,8 @@ def cpu_baseline(fat, lng, b, iters_full, sample_iters=3):
 
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, world, local_rank):
+    global CHOSEN
+    CHOSEN = args.chosen
     import numpy as np
     import torch
 
@@ -299,6 +301,8 @@ def run_gpu(args, rank, world, local_rank):
         barrier(world)
     launches = stag.stag_launch_count() - launches0
     shapes = {k: stag.stag_tuned_shape(h, MODE_PREC[CHOSEN], i) for i, k in enumerate(("plain", "epilogue"))}
+    mrhs_shape = stag.stag_tuned_mrhs(h, MODE_PREC[CHOSEN], NSRC) if BATCHED else None
+    df_shape = stag.stag_tuned_shape(h, "df64", 0)
     n_d, ms_d = stag.stag_profile_read(fam_plain)
     n_e, ms_e = stag.stag_profile_read(fam_epi)
     # one more (untimed) step with every launch of every family timed: where
@@ -346,13 +350,12 @@ def run_gpu(args, rank, world, local_rank):
     ok = all(i["converged"] and i["true_rel_resid"] <= TOL for i in infos_all + plain_infos)
     prec = MODE_PREC[CHOSEN]
     per_launch_ms = ms_d / max(n_d, 1)
-    pbits = {"fp32": 32, "fp16": 16, "fx16": 15, "fp64": 64}[prec]
+    pbits = {"fp32": 32, "fp16": 16, "fx16": 15, "fp64": 64, "fx16l": 31}[prec]
     nl = 6 if RECON == 12 else 9
     if BATCHED:
         # one launch: the links once and NSRC input and output vectors
         bytes_launch = ((8 * 9 + 8 * nl) * ELEM_BYTES[prec] + 2 * NSRC * VEC_BYTES[prec]) * Vh
-        capped = prec == "fp32" and NSRC <= 4  # the register-capped variant (six blocks per SM)
-        kernel_id = f"k_dslash_m{'_cap' if capped else ''}<{pbits},{nl},{NSRC}>"
+        kernel_id = f"k_dslash_mv<{pbits},{nl},{NSRC},{mrhs_shape[0]},{mrhs_shape[1]}>"
         sites_launch = NSRC * Vh
     else:
         bytes_launch = dslash_bytes_per_site(prec, RECON) * Vh
@@ -413,7 +416,11 @@ def run_gpu(args, rank, world, local_rank):
                 "avg_launch_us": per_launch_ms * 1e3,
                 "gflops": FLOP_PER_SITE * sites_launch / (per_launch_ms * 1e-3) / 1e9,
                 "epilogue_variant_avg_us": ms_e / max(n_e, 1) * 1e3,
-                "launch_shape": ({"multi_rhs": {"block": 128, "sites_per_thread": 1, "rhs_per_thread": NSRC}}
+                "launch_shape": ({"multi_rhs": {"block": 128, "threads_per_site": mrhs_shape[0],
+                                                "rhs_per_thread": NSRC // mrhs_shape[0],
+                                                "min_blocks_per_sm": mrhs_shape[1],
+                                                "tuned_us_per_operator": mrhs_shape[2],
+                                                "chosen_by": "autotuner (stag_tuned_mrhs)"}}
                                  if BATCHED else
                                  {k: {"block": v[0], "min_blocks_per_sm": v[1], "tuned_us": v[2]}
                                   for k, v in shapes.items()}),
@@ -425,7 +432,9 @@ def run_gpu(args, rank, world, local_rank):
                 "d2h_bytes_per_step": NSRC * vec_bytes,
             },
             "step_breakdown_ms": breakdown,
-            "reliable_update_operator": df_summary(breakdown, Vh, NSRC),
+            "reliable_update_operator": dict(df_summary(breakdown, Vh, NSRC) or {},
+                                             launch_shape={"block": 128, "threads_per_site": df_shape[1],
+                                                           "tuned_us": df_shape[2]}),
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -515,7 +524,8 @@ def run_dslash_sweep(args):
             for prec in args.sweep_precs:
                 if prec in ("fp64", "df64") and recon == 12:
                     continue
-                h = stag.stag_load_links(dims, fd, ld, recon_long=recon, prec_mask=1 << stag.PREC[prec])
+                copy = "fx16" if prec == "fx16l" else prec  # the hybrid reads the fixed-point link copy
+                h = stag.stag_load_links(dims, fd, ld, recon_long=recon, prec_mask=1 << stag.PREC[copy])
                 for nrhs in args.sweep_nrhs:
                     psi = torch.from_numpy(synth.random_spinor(dims, 3)).cuda()
                     if nrhs > 1:
@@ -906,6 +916,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chosen", default=CHOSEN, choices=sorted(MODE_PREC),
+                    help="solver mode of the timed step (the 4 sources batched)")
     ap.add_argument("--dslash-sweep", action="store_true", help="Dslash bandwidth sweep instead of the solve")
     ap.add_argument("--sweep-dims", nargs="+", default=["8", "16", "24", "32", "40", "48", "48x48x48x96"])
     ap.add_argument("--sweep-precs", nargs="+", default=["fp64", "fp32", "fp16", "fx16"])

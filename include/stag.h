@@ -61,8 +61,20 @@ extern "C" {
  * fraction of its FP32 rate).  Relative error of the operator about 1e-14.
  * The mixed-precision solvers compute their reliable updates (the true
  * residual b - M y) in this format when the handle holds its link copy, and
- * in FP64 otherwise. */
-typedef enum { STAG_FP64 = 0, STAG_FP32 = 1, STAG_FP16 = 2, STAG_FX16 = 3, STAG_DF64 = 4 } stag_prec;
+ * in FP64 otherwise.
+ * STAG_FX16L32: the 16-bit fixed-point links of the STAG_FX16 copy with FP32
+ * vectors and FP32 arithmetic (no copy of its own; the link bytes, the bulk
+ * of a multi-right-hand-side operator's traffic, halve while the vectors keep
+ * single precision).  Accepted by stag_dslash and stag_apply_m; the Krylov
+ * operator of STAG_MIXED16L. */
+typedef enum {
+  STAG_FP64 = 0,
+  STAG_FP32 = 1,
+  STAG_FP16 = 2,
+  STAG_FX16 = 3,
+  STAG_DF64 = 4,
+  STAG_FX16L32 = 5
+} stag_prec;
 
 /* Solver modes (the paper: QUDA's mixed-precision solvers, Sec. 3; single
  * precision about twice as fast as double, Sec. 4).  PLAIN64: every
@@ -78,10 +90,12 @@ typedef enum {
   STAG_MIXED32 = 1,
   STAG_MIXED16 = 2,
   STAG_MIXEDFX16 = 3,
-  STAG_LEARNED = 4  /* flexible CG preconditioned by a trained network (params->precond);
-                       sloppy operator in 16-bit fixed point if the handle holds that
-                       copy, else FP32; falls back to mixed CG if FCG breaks down or
-                       reaches max_iter */
+  STAG_LEARNED = 4,  /* flexible CG preconditioned by a trained network (params->precond);
+                        sloppy operator in 16-bit fixed point if the handle holds that
+                        copy, else FP32; falls back to mixed CG if FCG breaks down or
+                        reaches max_iter */
+  STAG_MIXED16L = 5  /* as MIXED32 with the STAG_FX16L32 operator: 16-bit fixed-point
+                        links, FP32 vectors (needs the STAG_FX16 copy) */
 } stag_mode;
 
 typedef struct stag_lattice_s* stag_lattice_t; /* opaque, library-owned */
@@ -146,7 +160,9 @@ int stag_free_lattice(stag_lattice_t lat);
  * minimum resident blocks per SM given to the compiler, and its timing in us
  * per launch (0 when not tuned).  For STAG_DF64 (four right-hand sides per
  * launch) min_blocks reports the threads that share a site's right-hand
- * sides (1, 2 or 4).  Any output pointer may be NULL. */
+ * sides (1, 2 or 4).  STAG_FX16L32 reports the shape tuned for STAG_FX16,
+ * which its single-right-hand-side kernels share.  Any output pointer may be
+ * NULL. */
 int stag_tuned_shape(stag_lattice_t lat, int prec, int kernel, int* block, int* min_blocks, double* us);
 
 /* The launch variant of the N-right-hand-side Dslash kernels (the operator
@@ -383,6 +399,73 @@ int stag_net_loss_grad(stag_net_t net, stag_lattice_t lat, const void* r, const 
 int stag_net_train(stag_net_t net, const stag_train_pair* pairs, int npairs, const stag_train_params* tp,
                    double* losses, void* stream);
 
+/* ------------------------------------------- one lattice over several ranks
+ * The paper's multi-node study (Sec. 4.1, Figs. 2-3: weak scaling of the
+ * staggered CG on KNL clusters, network-bound below about L = 30 per node;
+ * MILC moves neighbouring fields with gathers, Sec. 2) splits one lattice
+ * across nodes.  Here the lattice is split along t: rank r of R owns the
+ * global time slices [r T, (r + 1) T), T = Lt / R, which must be even and
+ * >= 4.  Each rank's handle holds the links of an extended slab of T + 2 H
+ * slices (H = STAG_DD_HALO): global slices r T - H .. r T + T + H - 1,
+ * periodic in t, local slice t' = t - r T + H (canonical [V_ext][4][3][3]
+ * complex double, V_ext = Lx Ly Lz (T + 2 H)).  Vectors are the rank's own
+ * sites: [Lx Ly Lz T / 2][3] complex double, local index lex_local / 2 with
+ * lex_local = x + Lx (y + Ly (z + Lz (t - r T))); a rank's even sites are
+ * the global even sites.  Each application of D first exchanges the three
+ * outermost own slices with the ranks above and below (the reach of the
+ * Naik hops) through the caller's communicator; CG sums its inner products
+ * over ranks through it.  FP64 (PLAIN64) only. */
+#define STAG_DD_HALO 4
+
+/* The caller's communicator.  Both calls get `stream`, the library's stream;
+ * they must finish (or queue on `stream`) their transfers before any work
+ * queued on `stream` after they return runs, and must wait for the work
+ * already queued on `stream` before reading device memory (e.g.
+ * cudaStreamSynchronize).  Return 0 on success.
+ *   exchange     : send `bytes` from send_lo to the rank below (r - 1 mod R)
+ *                  and from send_hi to the rank above (r + 1 mod R); receive
+ *                  the rank below's send_hi into recv_lo and the rank above's
+ *                  send_lo into recv_hi.  All four are device pointers into
+ *                  the library's fields (contiguous).  With R = 1 the rank is
+ *                  its own neighbour (periodic wrap).
+ *   allreduce_sum: replace the n doubles at `values` (device) by their sum
+ *                  over all ranks. */
+typedef struct {
+  void* ctx;
+  int (*exchange)(void* ctx, const void* send_lo, const void* send_hi, void* recv_lo, void* recv_hi,
+                  unsigned long long bytes, void* stream);
+  int (*allreduce_sum)(void* ctx, double* values, int n, void* stream);
+} stag_comm;
+
+typedef struct stag_dd_s* stag_dd_t;
+
+/* A rank's handle: gdims the global extents (even, >= 4), fat_ext/lng_ext
+ * the extended slab's links (device, copied), opts as for stag_load_links
+ * (an FP64 copy is built whatever prec_mask says).  EINVAL if Lt is not a
+ * multiple of nranks or T = Lt / nranks is odd or below 4.  Synchronises. */
+int stag_dd_create(stag_dd_t* out, const int gdims[4], int rank, int nranks, const void* fat_ext, const void* lng_ext,
+                   const stag_link_opts* opts, void* stream);
+int stag_dd_free(stag_dd_t d);
+/* The rank's own extents {Lx, Ly, Lz, T}, its sites per parity and the
+ * global t of its first slice.  Any output may be NULL. */
+int stag_dd_info(stag_dd_t d, int local_dims[4], long long* vh_local, int* t_offset);
+/* out = D in on the rank's own sites of parity out_parity (in: own sites of
+ * the other parity).  Every rank must call it (it exchanges).  Synchronous
+ * as far as the communicator is. */
+int stag_dd_dslash(stag_dd_t d, void* out, const void* in, int out_parity, const stag_comm* comm, void* stream);
+/* out = m^2 in - D_eo D_oe in on the rank's own even sites (two exchanges). */
+int stag_dd_apply_m(stag_dd_t d, void* out, const void* in, double mass, const stag_comm* comm, void* stream);
+/* FP64 CG on the split lattice (params->mode must be STAG_PLAIN64; tol,
+ * max_iter, use_initial_guess, check_interval as for stag_cg): per
+ * iteration two exchanges and two sums over ranks; when the iterated
+ * residual reaches the target the true residual b - M x (summed over ranks)
+ * decides, and CG restarts from it if it misses (info->reliable_updates
+ * counts these checks).  x, b: the rank's own even sites.  Every rank must
+ * call it with the same params; all ranks return the same status.
+ * Synchronises `stream`. */
+int stag_dd_cg(stag_dd_t d, void* x, const void* b, double mass, const stag_solve_params* params,
+               stag_solve_info* info, const stag_comm* comm, void* stream);
+
 /* Link construction before the operator (the paper's production code smears
  * the thin links before the solver: HISQ-link smearing, Sec. 1 and Sec. 2,
  * Fig. 1; the workload uses the three-staple fat link and the Naik link):
@@ -480,6 +563,18 @@ int stag_profile_reset(void);
 int stag_profile_read(const char* family, long long* launches, double* total_ms);
 /* All library kernel launches since the last reset. */
 long long stag_launch_count(void);
+
+/* The bounds-checked build (libstag_debug.so, compiled with
+ * -DSTAG_DEBUG_BOUNDS; compute-sanitizer is not available to this library's
+ * tests) checks every neighbour index of the stencil, every site index of a
+ * vector load or store and the site index of every link load against its
+ * extent; an out-of-range index is counted, the access redirected to index
+ * 0, and the kernel completes.  *count: violations since the last clear
+ * (waits for the device first), *first_code the kind of the first one (1:
+ * neighbour, 2: vector site, 3: link site) and *first_index its index;
+ * clear != 0 resets the records.  The normal build reports *count = -1.
+ * No counterpart in the paper. */
+int stag_bounds_violations(long long* count, int* first_code, long long* first_index, int clear);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,9 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libstag.so")
+# STAG_LIBRARY may name another build of the library (the bounds-checked
+# libstag_debug.so next to this file); default libstag.so
+LIB_PATH = os.environ.get("STAG_LIBRARY") or os.path.join(_HERE, "libstag.so")
 
 STAG_OK = 0
 STAG_EINVAL = -1
@@ -30,16 +32,18 @@ STAG_EBREAKDOWN = -5
 STAG_ENOTUNITARY = -6
 STAG_ETIMEOUT = -7
 
-STAG_FP64, STAG_FP32, STAG_FP16, STAG_FX16, STAG_DF64 = 0, 1, 2, 3, 4
-STAG_PLAIN64, STAG_MIXED32, STAG_MIXED16, STAG_MIXEDFX16, STAG_LEARNED = 0, 1, 2, 3, 4
+STAG_FP64, STAG_FP32, STAG_FP16, STAG_FX16, STAG_DF64, STAG_FX16L32 = 0, 1, 2, 3, 4, 5
+STAG_PLAIN64, STAG_MIXED32, STAG_MIXED16, STAG_MIXEDFX16, STAG_LEARNED, STAG_MIXED16L = 0, 1, 2, 3, 4, 5
 
-PREC = {"fp64": STAG_FP64, "fp32": STAG_FP32, "fp16": STAG_FP16, "fx16": STAG_FX16, "df64": STAG_DF64}
+PREC = {"fp64": STAG_FP64, "fp32": STAG_FP32, "fp16": STAG_FP16, "fx16": STAG_FX16, "df64": STAG_DF64,
+        "fx16l": STAG_FX16L32}
 MODE = {
     "plain64": STAG_PLAIN64,
     "mixed32": STAG_MIXED32,
     "mixed16": STAG_MIXED16,
     "mixedfx16": STAG_MIXEDFX16,
     "learned": STAG_LEARNED,
+    "mixed16l": STAG_MIXED16L,
 }
 
 # every entry point declared in include/stag.h
@@ -81,6 +85,13 @@ EXPORTS = (
     "stag_tune_cache_save",
     "stag_tune_cache_clear",
     "stag_tune_cache_size",
+    "stag_dd_create",
+    "stag_dd_free",
+    "stag_dd_info",
+    "stag_dd_dslash",
+    "stag_dd_apply_m",
+    "stag_dd_cg",
+    "stag_bounds_violations",
 )
 
 
@@ -208,6 +219,14 @@ def load_library(path=LIB_PATH):
         "stag_tune_cache_save": (ci, [ctypes.c_char_p]),
         "stag_tune_cache_clear": (ci, []),
         "stag_tune_cache_size": (ctypes.c_longlong, []),
+        "stag_dd_create": (ci, [ctypes.POINTER(vp), ctypes.POINTER(ci), ci, ci, vp, vp, ctypes.POINTER(LinkOpts), vp]),
+        "stag_dd_free": (ci, [vp]),
+        "stag_dd_info": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ci)]),
+        "stag_dd_dslash": (ci, [vp, vp, vp, ci, vp, vp]),
+        "stag_dd_apply_m": (ci, [vp, vp, vp, cd, vp, vp]),
+        "stag_dd_cg": (ci, [vp, vp, vp, cd, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo), vp, vp]),
+        "stag_bounds_violations": (ci, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ci),
+                                        ctypes.POINTER(ctypes.c_longlong), ci]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -627,3 +646,221 @@ def stag_tune_cache_clear():
 
 def stag_tune_cache_size():
     return int(_lib.stag_tune_cache_size())
+
+
+# ---------------------------------------------------------------- one lattice over several ranks
+DD_HALO = 4  # STAG_DD_HALO
+
+_EXCH_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_void_p)
+_ALLRED_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                              ctypes.c_void_p)
+
+
+class StagComm(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("exchange", _EXCH_FN), ("allreduce_sum", _ALLRED_FN)]
+
+
+class _CudaBytes:
+    """A raw device range seen by torch without a copy (__cuda_array_interface__)."""
+
+    def __init__(self, ptr, n, typestr="|u1"):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+def _view(ptr, nbytes, dtype=torch.uint8):
+    typestr = {torch.uint8: "|u1", torch.float64: "<f8"}[dtype]
+    n = nbytes // (8 if dtype == torch.float64 else 1)
+    return torch.as_tensor(_CudaBytes(ptr, n, typestr), device="cuda")
+
+
+class Communicator:
+    """The caller side of stag_comm: subclasses implement
+
+      exchange(send_lo, send_hi, recv_lo, recv_hi)  uint8 CUDA tensors: send_lo
+          to the rank below, send_hi to the rank above, receive the rank
+          below's send_hi into recv_lo and the rank above's send_lo into recv_hi
+      allreduce(t)                                   float64 CUDA tensor, in place
+
+    The library's callbacks wrap the raw device ranges as tensors and run the
+    subclass's work on the library's stream (so it is ordered after the
+    kernels that wrote the data and before those that read the result)."""
+
+    def __init__(self, rank, size):
+        self.rank, self.size = int(rank), int(size)
+        self.error = None
+        self._ex = _EXCH_FN(self._exchange_cb)
+        self._ar = _ALLRED_FN(self._allreduce_cb)
+        self.struct = StagComm(None, self._ex, self._ar)
+
+    def _exchange_cb(self, ctx, slo, shi, rlo, rhi, nbytes, stream):
+        try:
+            st = torch.cuda.ExternalStream(int(stream)) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(st):
+                self.exchange(*[_view(p, nbytes) for p in (slo, shi, rlo, rhi)])
+            return 0
+        except Exception as e:  # reported as a failed call (STAG_ECUDA); kept for the caller
+            self.error = e
+            return 1
+
+    def _allreduce_cb(self, ctx, values, n, stream):
+        try:
+            st = torch.cuda.ExternalStream(int(stream)) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(st):
+                self.allreduce(_view(ctypes.cast(values, ctypes.c_void_p).value, 8 * n, torch.float64))
+            return 0
+        except Exception as e:
+            self.error = e
+            return 1
+
+
+class TorchDistComm(Communicator):
+    """stag_comm over torch.distributed (default group): NCCL moves the
+    device buffers directly; gloo stages them through host memory.  The
+    halo sent to the rank below travels with tag 1, the one sent above with
+    tag 2, so that two ranks (each the other's lower and upper neighbour)
+    keep them apart."""
+
+    def __init__(self):
+        import torch.distributed as dist
+
+        super().__init__(dist.get_rank(), dist.get_world_size())
+        self.dist = dist
+        self.host = dist.get_backend() != "nccl"
+
+    def exchange(self, send_lo, send_hi, recv_lo, recv_hi):
+        dist, R, r = self.dist, self.size, self.rank
+        if R == 1:
+            recv_lo.copy_(send_hi)
+            recv_hi.copy_(send_lo)
+            return
+        lo, hi = (r - 1) % R, (r + 1) % R
+        if self.host:
+            s_lo, s_hi = send_lo.cpu(), send_hi.cpu()
+            b_lo, b_hi = torch.empty_like(s_lo), torch.empty_like(s_hi)
+            reqs = [dist.isend(s_lo, lo, tag=1), dist.isend(s_hi, hi, tag=2),
+                    dist.irecv(b_lo, lo, tag=2), dist.irecv(b_hi, hi, tag=1)]
+            for q in reqs:
+                q.wait()
+            recv_lo.copy_(b_lo)
+            recv_hi.copy_(b_hi)
+        else:
+            ops = [dist.P2POp(dist.isend, send_lo, lo), dist.P2POp(dist.isend, send_hi, hi),
+                   dist.P2POp(dist.irecv, recv_lo, lo), dist.P2POp(dist.irecv, recv_hi, hi)]
+            for q in dist.batch_isend_irecv(ops):
+                q.wait()
+
+    def allreduce(self, t):
+        if self.host:
+            h = t.cpu()
+            self.dist.all_reduce(h)
+            t.copy_(h)
+        else:
+            self.dist.all_reduce(t)
+
+
+class DDHandle:
+    """Owns a ``stag_dd_t`` (one rank's part of a lattice split along t)."""
+
+    def __init__(self, ptr, gdims, rank, nranks):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.gdims, self.rank, self.nranks = tuple(gdims), rank, nranks
+        d = (ctypes.c_int * 4)()
+        vh, t0 = ctypes.c_longlong(), ctypes.c_int()
+        _check(_lib.stag_dd_info(self.ptr, d, ctypes.byref(vh), ctypes.byref(t0)), "stag_dd_info")
+        self.local_dims, self.Vh, self.t_offset = tuple(d), vh.value, t0.value
+
+    def free(self):
+        if self.ptr and self.ptr.value:
+            _check(_lib.stag_dd_free(self.ptr), "stag_dd_free")
+            self.ptr = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def stag_dd_create(gdims, rank, nranks, fat_ext, lng_ext, recon_long=18, long_coeff=-1.0 / 24.0, stream=None):
+    """One rank's handle; fat_ext, lng_ext: the extended slab's links (see dd_slab), complex128 CUDA."""
+    g = tuple(int(v) for v in gdims)
+    T = g[3] // int(nranks)
+    n = g[0] * g[1] * g[2] * (T + 2 * DD_HALO) * 36
+    h = ctypes.c_void_p()
+    o = LinkOpts(int(recon_long), float(long_coeff), 1 << STAG_FP64, 1)
+    _check(_lib.stag_dd_create(ctypes.byref(h), (ctypes.c_int * 4)(*g), int(rank), int(nranks),
+                               _ptr(fat_ext, "fat_ext", n), _ptr(lng_ext, "lng_ext", n), ctypes.byref(o),
+                               _stream(stream)), "stag_dd_create")
+    return DDHandle(h.value, g, int(rank), int(nranks))
+
+
+def _dd_call(name, status, comm):
+    if status != STAG_OK:
+        err = StagError(status, name)
+        if comm.error is not None:
+            raise err from comm.error
+        raise err
+
+
+def stag_dd_dslash(dd, out, inp, out_parity, comm, stream=None):
+    n = dd.Vh * 3
+    st = _lib.stag_dd_dslash(dd.ptr, _ptr(out, "out", n), _ptr(inp, "inp", n), int(out_parity),
+                             ctypes.byref(comm.struct), _stream(stream))
+    _dd_call("stag_dd_dslash", st, comm)
+    return out
+
+
+def stag_dd_apply_m(dd, out, inp, mass, comm, stream=None):
+    n = dd.Vh * 3
+    st = _lib.stag_dd_apply_m(dd.ptr, _ptr(out, "out", n), _ptr(inp, "inp", n), float(mass),
+                              ctypes.byref(comm.struct), _stream(stream))
+    _dd_call("stag_dd_apply_m", st, comm)
+    return out
+
+
+def stag_dd_cg(dd, x, b, mass, comm, params=None, stream=None, raise_on_error=True, **kw):
+    """FP64 CG on the split lattice; x, b: the rank's own even sites.  Returns the info dict."""
+    kw.setdefault("mode", "plain64")
+    p = params if params is not None else default_params(**kw)
+    info = SolveInfo()
+    n = dd.Vh * 3
+    st = _lib.stag_dd_cg(dd.ptr, _ptr(x, "x", n), _ptr(b, "b", n), float(mass), ctypes.byref(p), ctypes.byref(info),
+                         ctypes.byref(comm.struct), _stream(stream))
+    if raise_on_error and st != STAG_OK:
+        _dd_call("stag_dd_cg", st, comm)
+    d = info.as_dict()
+    d["return"] = st
+    return d
+
+
+def dd_slab(links, gdims, rank, nranks):
+    """The extended slab of canonical [V][4][3][3] links a rank's handle takes:
+    global slices rank*T - DD_HALO .. rank*T + T + DD_HALO - 1, periodic in t
+    (works on numpy arrays and torch tensors of the global field)."""
+    Lx, Ly, Lz, Lt = (int(v) for v in gdims)
+    T = Lt // int(nranks)
+    slab = Lx * Ly * Lz
+    ts = [(rank * T - DD_HALO + k) % Lt for k in range(T + 2 * DD_HALO)]
+    shp = links.shape
+    per_t = links.reshape((Lt, slab) + tuple(shp[1:]))
+    idx = torch.tensor(ts) if isinstance(links, torch.Tensor) else ts
+    out = per_t[idx]
+    return out.reshape((len(ts) * slab,) + tuple(shp[1:]))
+
+
+def dd_own_sites(field, gdims, rank, nranks):
+    """A rank's own sites of a global single-parity field [V/2][3] (or [..][V/2][3])."""
+    Lx, Ly, Lz, Lt = (int(v) for v in gdims)
+    T = Lt // int(nranks)
+    S = Lx // 2 * Ly * Lz
+    return field[..., rank * T * S:(rank + 1) * T * S, :]
+
+
+def stag_bounds_violations(clear=False):
+    """(count, first code, first index) of the bounds-checked build; count -1 in the normal build."""
+    n, c, i = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_longlong()
+    _check(_lib.stag_bounds_violations(ctypes.byref(n), ctypes.byref(c), ctypes.byref(i), 1 if clear else 0),
+           "stag_bounds_violations")
+    return n.value, c.value, i.value

@@ -2,7 +2,9 @@
 
 Each .cu translation unit compiles in its own nvcc process (in parallel);
 the objects link into ``paper_1712_00143_gb300/libstag.so``.  Objects are
-rebuilt only when a source or header is newer than them.
+rebuilt only when a source or header is newer than them.  ``--debug-bounds``
+(or build(debug_bounds=True)) builds the bounds-checked
+``libstag_debug.so`` from the same sources with -DSTAG_DEBUG_BOUNDS.
 """
 
 import os
@@ -16,6 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstag.so")
+# the bounds-checked build (every global index checked, violations recorded)
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libstag_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + [
@@ -49,56 +54,62 @@ def _headers():
     return hs
 
 
-def _compile(src, extra, verbose):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src, extra, verbose, build_dir):
+    obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not extra:
         return obj, ""
-    cmd = [_nvcc()] + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
+    flags = list(extra)
+    if build_dir == BUILD_DEBUG:
+        flags.append("-DSTAG_DEBUG_BOUNDS")
+    cmd = [_nvcc()] + NVCC_FLAGS + flags + ["-c", src, "-o", obj]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{' '.join(cmd)}\n{p.stdout}\n{p.stderr}")
     return obj, (p.stdout + p.stderr) if verbose else ""
 
 
-def _stamp_ok():
+def _stamp_ok(build_dir):
     """Objects and library were built on this machine type (x86_64 / aarch64)."""
-    stamp = os.path.join(BUILD, "MACHINE")
+    stamp = os.path.join(build_dir, "MACHINE")
     try:
         return open(stamp).read().strip() == platform.machine()
     except OSError:
         return False
 
 
-def build(verbose=False, extra_flags=(), jobs=None):
-    """Compile every kernel source and link libstag.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
-    if not _stamp_ok():
-        for f in os.listdir(BUILD):
-            os.remove(os.path.join(BUILD, f))
-        if os.path.exists(LIB):
-            os.remove(LIB)
-        with open(os.path.join(BUILD, "MACHINE"), "w") as fh:
+def build(verbose=False, extra_flags=(), jobs=None, debug_bounds=False):
+    """Compile every kernel source and link libstag.so (debug_bounds: the
+    bounds-checked libstag_debug.so); returns the library path."""
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug_bounds else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
+    if not _stamp_ok(build_dir):
+        for f in os.listdir(build_dir):
+            os.remove(os.path.join(build_dir, f))
+        if os.path.exists(lib):
+            os.remove(lib)
+        with open(os.path.join(build_dir, "MACHINE"), "w") as fh:
             fh.write(platform.machine())
     srcs = _sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with ThreadPoolExecutor(max_workers=jobs) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra_flags, verbose), srcs))
+        results = list(ex.map(lambda s: _compile(s, extra_flags, verbose, build_dir), srcs))
     objs = [o for o, _ in results]
     for _, log in results:
         if log:
             sys.stderr.write(log)
-    if os.path.exists(LIB) and not extra_flags:
-        if os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
-            return LIB
-    tmp = LIB + ".tmp"
+    if os.path.exists(lib) and not extra_flags:
+        if os.path.getmtime(lib) >= max(os.path.getmtime(o) for o in objs):
+            return lib
+    tmp = lib + ".tmp"
     cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{p.stdout}\n{p.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else ()))
+    print(build(verbose="-v" in sys.argv, extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else (),
+                debug_bounds="--debug-bounds" in sys.argv))

@@ -228,6 +228,21 @@ void prof_discard_since(long long mark) {
   g_open.resize(keep);
 }
 
+// ------------------------------------------------------------ bounds records
+#ifdef STAG_DEBUG_BOUNDS
+namespace {
+struct BoundsTU {
+  int (*read)(unsigned long long*);
+  int (*clear)();
+};
+std::vector<BoundsTU>& bounds_registry() {
+  static std::vector<BoundsTU> r;
+  return r;
+}
+}  // namespace
+void bounds_register(int (*read)(unsigned long long*), int (*clear)()) { bounds_registry().push_back({read, clear}); }
+#endif
+
 }  // namespace stag
 
 using namespace stag;
@@ -295,6 +310,44 @@ int stag_profile_read(const char* family, long long* launches, double* total_ms)
 
 long long stag_launch_count(void) { return g_launches.load(); }
 
+int stag_bounds_violations(long long* count, int* first_code, long long* first_index, int clear) {
+  if (!count) return STAG_EINVAL;
+#ifdef STAG_DEBUG_BOUNDS
+  long long n = 0;
+  int code = 0;
+  long long index = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return STAG_ECUDA;
+  }
+  for (const auto& tu : bounds_registry()) {
+    unsigned long long v[3] = {0ull, 0ull, 0ull};
+    if (tu.read(v)) {
+      cudaGetLastError();
+      return STAG_ECUDA;
+    }
+    if (v[0] && !n) {
+      code = (int)v[1];
+      index = (long long)v[2];
+    }
+    n += (long long)v[0];
+    if (clear && v[0] && tu.clear()) {
+      cudaGetLastError();
+      return STAG_ECUDA;
+    }
+  }
+  *count = n;
+  if (first_code) *first_code = code;
+  if (first_index) *first_index = index;
+#else
+  (void)clear;
+  *count = -1;
+  if (first_code) *first_code = 0;
+  if (first_index) *first_index = 0;
+#endif
+  return STAG_OK;
+}
+
 int stag_load_links(stag_lattice_t* out, const int dims[4], const void* fat, const void* lng,
                     const stag_link_opts* opts, void* stream) {
   if (!out || !dims || !fat || !lng) return STAG_EINVAL;
@@ -352,7 +405,9 @@ int stag_free_lattice(stag_lattice_t lat) {
 }
 
 int stag_tuned_shape(stag_lattice_t lat, int prec, int kernel, int* block, int* min_blocks, double* us) {
-  if (!lat || prec < 0 || prec > 4 || kernel < 0 || kernel > 1 || !lat->links[prec].present) return STAG_EINVAL;
+  if (!lat || prec < 0 || prec > STAG_FX16L32 || kernel < 0 || kernel > 1) return STAG_EINVAL;
+  prec = link_copy_of(prec);  // the single-RHS STAG_FX16L32 kernels run in the shapes tuned for STAG_FX16
+  if (!lat->links[prec].present) return STAG_EINVAL;
   const LinkCopy& L = lat->links[prec];
   int v = kernel == 0 ? L.shape_plain : L.shape_epi;
   if (prec == STAG_DF64) {
@@ -392,6 +447,7 @@ template Spinor<64> ws_spinor<64>(stag_lattice_s*, const std::string&, int*);
 template Spinor<32> ws_spinor<32>(stag_lattice_s*, const std::string&, int*);
 template Spinor<16> ws_spinor<16>(stag_lattice_s*, const std::string&, int*);
 template Spinor<15> ws_spinor<15>(stag_lattice_s*, const std::string&, int*);
+template Spinor<31> ws_spinor<31>(stag_lattice_s*, const std::string&, int*);
 
 template <int P>
 static int dslash_p(stag_lattice_s* lat, double2* out, const double2* in, int out_parity, int nrhs, cudaStream_t st) {
@@ -461,11 +517,12 @@ extern "C" {
 
 int stag_dslash(stag_lattice_t lat, void* out, const void* in, int out_parity, int prec, int nrhs, void* stream) {
   if (!lat || !out || !in || (out_parity != 0 && out_parity != 1) || nrhs < 1) return STAG_EINVAL;
-  if (prec < 0 || prec > 4 || !lat->links[prec].present) return STAG_EINVAL;
+  if (prec < 0 || prec > STAG_FX16L32 || !lat->links[link_copy_of(prec)].present) return STAG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == STAG_DF64) return dslash_df_canonical(lat, (double2*)out, (const double2*)in, out_parity, nrhs, st);
   if (nrhs > 1) return dslash_multi(lat, (double2*)out, (const double2*)in, out_parity, prec, nrhs, st);
   switch (prec) {
+    case STAG_FX16L32: return dslash_p<31>(lat, (double2*)out, (const double2*)in, out_parity, nrhs, st);
     case STAG_FP64: return dslash_p<64>(lat, (double2*)out, (const double2*)in, out_parity, nrhs, st);
     case STAG_FP32: return dslash_p<32>(lat, (double2*)out, (const double2*)in, out_parity, nrhs, st);
     case STAG_FP16: return dslash_p<16>(lat, (double2*)out, (const double2*)in, out_parity, nrhs, st);
@@ -475,11 +532,12 @@ int stag_dslash(stag_lattice_t lat, void* out, const void* in, int out_parity, i
 
 int stag_apply_m(stag_lattice_t lat, void* out, const void* in, double mass, double shift, int prec, void* stream) {
   if (!lat || !out || !in) return STAG_EINVAL;
-  if (prec < 0 || prec > 4 || !lat->links[prec].present) return STAG_EINVAL;
+  if (prec < 0 || prec > STAG_FX16L32 || !lat->links[link_copy_of(prec)].present) return STAG_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   double a = mass * mass + shift;
   if (prec == STAG_DF64) return apply_m_df(lat, (double2*)out, (const double2*)in, a, st);
   switch (prec) {
+    case STAG_FX16L32: return apply_m_p<31>(lat, (double2*)out, (const double2*)in, a, st);
     case STAG_FP64: return apply_m_p<64>(lat, (double2*)out, (const double2*)in, a, st);
     case STAG_FP32: return apply_m_p<32>(lat, (double2*)out, (const double2*)in, a, st);
     case STAG_FP16: return apply_m_p<16>(lat, (double2*)out, (const double2*)in, a, st);

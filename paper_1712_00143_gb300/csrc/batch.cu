@@ -99,7 +99,7 @@ static int dslash_multi_p(stag_lattice_s* lat, double2* out, const double2* in, 
     else break;
     if (s) return s;
   }
-  if (r < nrhs) return stag_dslash(lat, out + r * n, in + r * n, out_parity, prec_index<P>(), 1, st);
+  if (r < nrhs) return stag_dslash(lat, out + r * n, in + r * n, out_parity, P == 31 ? STAG_FX16L32 : prec_index<P>(), 1, st);
   return STAG_OK;
 }
 
@@ -109,6 +109,7 @@ int dslash_multi(stag_lattice_s* lat, double2* out, const double2* in, int out_p
     case STAG_FP64: return dslash_multi_p<64>(lat, out, in, out_parity, nrhs, st);
     case STAG_FP32: return dslash_multi_p<32>(lat, out, in, out_parity, nrhs, st);
     case STAG_FP16: return dslash_multi_p<16>(lat, out, in, out_parity, nrhs, st);
+    case STAG_FX16L32: return dslash_multi_p<31>(lat, out, in, out_parity, nrhs, st);
     default: return dslash_multi_p<15>(lat, out, in, out_parity, nrhs, st);
   }
 }
@@ -810,7 +811,8 @@ extern "C" int stag_batch_solve(const stag_batch_item* items, int nitems, const 
   stag_solve_params prm;
   stag_default_params(&prm);
   if (params) prm = *params;
-  if (!(prm.tol > 0.0) || prm.max_iter < 0 || prm.mode < 0 || prm.mode > 3) return STAG_EINVAL;  // no learned mode
+  if (!(prm.tol > 0.0) || prm.max_iter < 0 || prm.mode < 0 || prm.mode > STAG_MIXED16L || prm.mode == STAG_LEARNED)
+    return STAG_EINVAL;  // no learned mode
   if (prm.mode != STAG_PLAIN64 && !(prm.delta > 0.0 && prm.delta < 1.0)) return STAG_EINVAL;
   const int pi = prm.mode == STAG_PLAIN64 ? STAG_FP64 : prm.mode == STAG_MIXED32 ? STAG_FP32
                : prm.mode == STAG_MIXED16 ? STAG_FP16 : STAG_FX16;
@@ -824,6 +826,7 @@ extern "C" int stag_batch_solve(const stag_batch_item* items, int nitems, const 
     case STAG_PLAIN64: return batch_solve_p<64>(items, nitems, prm, infos, st);
     case STAG_MIXED32: return batch_solve_p<32>(items, nitems, prm, infos, st);
     case STAG_MIXED16: return batch_solve_p<16>(items, nitems, prm, infos, st);
+    case STAG_MIXED16L: return batch_solve_p<31>(items, nitems, prm, infos, st);
     default: return batch_solve_p<15>(items, nitems, prm, infos, st);
   }
 }

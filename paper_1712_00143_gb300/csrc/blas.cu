@@ -458,6 +458,9 @@ STAG_BLAS_P(64)
 STAG_BLAS_P(32)
 STAG_BLAS_P(16)
 STAG_BLAS_P(15)
+STAG_BLAS_P(31)
+template int launch_convert<31, 64>(Spinor<31>, Spinor<64>, cudaStream_t);
+template int launch_convert<31, 32>(Spinor<31>, Spinor<32>, cudaStream_t);
 template int launch_accumulate<64>(Spinor<64>, Spinor<64>, cudaStream_t);
 template int launch_accumulate<32>(Spinor<64>, Spinor<32>, cudaStream_t);
 template int launch_convert<32, 64>(Spinor<32>, Spinor<64>, cudaStream_t);

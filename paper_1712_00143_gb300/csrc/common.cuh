@@ -9,6 +9,46 @@
 
 namespace stag {
 
+// ------------------------------------------------------------------ bounds-checked build
+// Built with -DSTAG_DEBUG_BOUNDS (libstag_debug.so), the index computations
+// that address global memory -- every neighbour index of the stencil, every
+// site index of a vector load or store, the site index of every link load --
+// are checked against their extent; a violation is counted in a device word
+// (with the first one's code and index) and the access goes to index 0
+// instead, so the kernel completes and the host reads the record
+// (stag_bounds_violations).  Every translation unit has its own record,
+// registered with the host at load time.  The normal build compiles the
+// checks away.
+#ifdef STAG_DEBUG_BOUNDS
+void bounds_register(int (*read)(unsigned long long*), int (*clear)());
+namespace {
+__device__ unsigned long long g_bounds[3];  // violations, first code, first index
+__device__ __forceinline__ long long bounds_check(long long idx, long long n, int code) {
+  if (idx >= 0 && idx < n) return idx;
+  if (atomicAdd(&g_bounds[0], 1ull) == 0ull) {
+    g_bounds[1] = (unsigned long long)code;
+    g_bounds[2] = (unsigned long long)idx;
+  }
+  return 0;
+}
+inline int bounds_read_tu(unsigned long long* v) {
+  return cudaMemcpyFromSymbol(v, g_bounds, sizeof(g_bounds)) == cudaSuccess ? 0 : 1;
+}
+inline int bounds_clear_tu() {
+  const unsigned long long z[3] = {0ull, 0ull, 0ull};
+  return cudaMemcpyToSymbol(g_bounds, z, sizeof(z)) == cudaSuccess ? 0 : 1;
+}
+struct BoundsReg {
+  BoundsReg() { bounds_register(&bounds_read_tu, &bounds_clear_tu); }
+} g_bounds_reg;
+}  // namespace
+#define STAG_BOUND(idx, n, code) ((int)::stag::bounds_check((long long)(idx), (long long)(n), (code)))
+#else
+#define STAG_BOUND(idx, n, code) (idx)
+#endif
+// codes of the checked index kinds
+enum BoundCode : int { BOUND_NEIGHBOUR = 1, BOUND_VECTOR = 2, BOUND_LINK = 3 };
+
 // ------------------------------------------------------------------ geometry
 // Checkerboard (single-parity) index s of a site = lex/2, lex = x + Lx*(y +
 // Ly*(z + Lz*t)).  With Lx even, s = x/2 + Lxh*(y + Ly*(z + Lz*t)), so a
@@ -73,13 +113,16 @@ __device__ __forceinline__ Coord cb_coords(const Geom& g, int s, int parity) {
 __device__ __forceinline__ int wrapc(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
 
 // Checkerboard index of the site c + k*mu (k in {-3,-1,1,3}); s is c's own index.
-__device__ __forceinline__ int cb_neighbour(const Geom& g, int s, const Coord& c, int mu, int k) {
+__device__ __forceinline__ int cb_neighbour_raw(const Geom& g, int s, const Coord& c, int mu, int k) {
   switch (mu) {
     case 0: return s - (c.x >> 1) + (wrapc(c.x + k, g.L[0]) >> 1);
     case 1: return s + (wrapc(c.y + k, g.L[1]) - c.y) * g.sy;
     case 2: return s + (wrapc(c.z + k, g.L[2]) - c.z) * g.sz;
     default: return s + (wrapc(c.t + k, g.L[3]) - c.t) * g.st;
   }
+}
+__device__ __forceinline__ int cb_neighbour(const Geom& g, int s, const Coord& c, int mu, int k) {
+  return STAG_BOUND(cb_neighbour_raw(g, s, c, mu, k), g.Vh, BOUND_NEIGHBOUR);
 }
 
 // Staggered phase eta_mu(x) as a sign bit: 1 means -1.
@@ -143,6 +186,14 @@ template <> struct Prec<15> {
   using A2 = float2;
 };
 
+// Tag 31: 16-bit fixed-point links (the storage of tag 15) with FP32 vectors
+// and arithmetic (those of tag 32): the link bytes, the bulk of a multi-RHS
+// operator's traffic, halve while the vectors keep single precision.
+template <> struct Prec<31> : Prec<32> {};
+
+// Links stored as 16-bit fixed point (integers in units of a per-field scale).
+__host__ __device__ constexpr bool fixed_links(int p) { return p == 15 || p == 31; }
+
 constexpr float FX_ONE = 32767.0f;  // fixed-point full scale
 
 // ---- 16-byte link chunks: complex numbers packed PER to a 16-byte word so
@@ -196,6 +247,7 @@ template <> struct Chunk<15> {
     return short2_bits_to_float2(word_of(c, lane));
   }
 };
+template <> struct Chunk<31> : Chunk<15> {};
 
 // A single-parity colour-vector field in the internal layout:
 //   P = 64: [Vh][3] double2 (array of structures, the canonical layout)
@@ -211,22 +263,25 @@ template <int P> struct Spinor {
 };
 
 template <int P> __host__ __device__ inline size_t spinor_bytes(int Vh) {
-  return P == 64 ? (size_t)Vh * 48 : P == 32 ? (size_t)Vh * 24 : (size_t)Vh * 16;
+  return P == 64 ? (size_t)Vh * 48 : (P == 32 || P == 31) ? (size_t)Vh * 24 : (size_t)Vh * 16;
 }
 
 template <int P> struct SpinorLoad;
 template <> struct SpinorLoad<64> {
   static __device__ __forceinline__ void ld(const Spinor<64>& f, int s, double2 o[3]) {
+    s = STAG_BOUND(s, f.Vh, BOUND_VECTOR);
     const double2* p = (const double2*)f.v + 3 * (size_t)s;
 #pragma unroll
     for (int c = 0; c < 3; ++c) o[c] = __ldg(p + c);
   }
   static __device__ __forceinline__ void ldw(const Spinor<64>& f, int s, double2 o[3]) {
+    s = STAG_BOUND(s, f.Vh, BOUND_VECTOR);
     const double2* p = (const double2*)f.v + 3 * (size_t)s;
 #pragma unroll
     for (int c = 0; c < 3; ++c) o[c] = p[c];
   }
   static __device__ __forceinline__ void st(const Spinor<64>& f, int s, const double2 o[3]) {
+    s = STAG_BOUND(s, f.Vh, BOUND_VECTOR);
     double2* p = (double2*)f.v + 3 * (size_t)s;
 #pragma unroll
     for (int c = 0; c < 3; ++c) p[c] = o[c];
@@ -234,26 +289,41 @@ template <> struct SpinorLoad<64> {
 };
 template <> struct SpinorLoad<32> {
   static __device__ __forceinline__ void ld(const Spinor<32>& f, int s, float2 o[3]) {
+    s = STAG_BOUND(s, f.Vh, BOUND_VECTOR);
     const float2* p = (const float2*)f.v;
 #pragma unroll
     for (int c = 0; c < 3; ++c) o[c] = __ldg(p + c * (size_t)f.Vh + s);
   }
   static __device__ __forceinline__ void ldw(const Spinor<32>& f, int s, float2 o[3]) {
+    s = STAG_BOUND(s, f.Vh, BOUND_VECTOR);
     const float2* p = (const float2*)f.v;
 #pragma unroll
     for (int c = 0; c < 3; ++c) o[c] = p[c * (size_t)f.Vh + s];
   }
   static __device__ __forceinline__ void st(const Spinor<32>& f, int s, const float2 o[3]) {
+    s = STAG_BOUND(s, f.Vh, BOUND_VECTOR);
     float2* p = (float2*)f.v;
 #pragma unroll
     for (int c = 0; c < 3; ++c) p[c * (size_t)f.Vh + s] = o[c];
   }
 };
 
+// FP32 vectors of the fixed-point-link format (tag 31)
+template <> struct SpinorLoad<31> {
+  static __device__ __forceinline__ Spinor<32> as32(const Spinor<31>& f) { return Spinor<32>{f.v, f.Vh}; }
+  static __device__ __forceinline__ void ld(const Spinor<31>& f, int s, float2 o[3]) { SpinorLoad<32>::ld(as32(f), s, o); }
+  static __device__ __forceinline__ void ldw(const Spinor<31>& f, int s, float2 o[3]) {
+    SpinorLoad<32>::ldw(as32(f), s, o);
+  }
+  static __device__ __forceinline__ void st(const Spinor<31>& f, int s, const float2 o[3]) {
+    SpinorLoad<32>::st(as32(f), s, o);
+  }
+};
+
 // L2 prefetch of one site's vector (no registers): issued at the start of a
 // kernel whose epilogue reads the vector only after a long computation.
 template <int P> __device__ __forceinline__ void prefetch_spinor_l2(const Spinor<P>& f, int s) {
-  if constexpr (P == 32) {
+  if constexpr (P == 32 || P == 31) {
     const float2* p = (const float2*)f.v;
 #pragma unroll
     for (int c = 0; c < 3; ++c) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + c * (size_t)f.Vh + s));
@@ -278,10 +348,10 @@ template <int P> struct SpinorLoad16 {
     o[2] = make_float2(c.x * k, c.y * k);
   }
   static __device__ __forceinline__ void ld(const Spinor<P>& f, int s, float2 o[3]) {
-    unpack(__ldg((const uint4*)f.v + s), o);
+    unpack(__ldg((const uint4*)f.v + STAG_BOUND(s, f.Vh, BOUND_VECTOR)), o);
   }
   static __device__ __forceinline__ void ldw(const Spinor<P>& f, int s, float2 o[3]) {
-    unpack(((const uint4*)f.v)[s], o);
+    unpack(((const uint4*)f.v)[STAG_BOUND(s, f.Vh, BOUND_VECTOR)], o);
   }
   static __device__ __forceinline__ unsigned pack2(float x, float y) {
     if (P == 16) {
@@ -305,7 +375,7 @@ template <int P> struct SpinorLoad16 {
     r.y = pack2(o[1].x * inv, o[1].y * inv);
     r.z = pack2(o[2].x * inv, o[2].y * inv);
     r.w = __float_as_uint(m / full);
-    ((uint4*)f.v)[s] = r;
+    ((uint4*)f.v)[STAG_BOUND(s, f.Vh, BOUND_VECTOR)] = r;
   }
 };
 template <> struct SpinorLoad<16> : SpinorLoad16<16> {};

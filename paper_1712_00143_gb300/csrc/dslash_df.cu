@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(DFB) k_dslash_df(DfArgs a, const int* stop) {
       // hop order of the link layout: +mu, -mu (fat), +3mu, -3mu (Naik)
       const int k = h == 0 ? 1 : h == 1 ? -1 : h == 2 ? 3 : -3;
       const int nb = cb_neighbour(a.g, s, c, mu, k);
-      const float4* L = a.links + (size_t)(mu * 36 + h * 9) * Vh + s;
+      const float4* L = a.links + (size_t)(mu * 36 + h * 9) * Vh + STAG_BOUND(s, Vh, BOUND_LINK);
       const float4* pin = a.in + 3 * (size_t)nb;
       // column by column: one link column (3 entries) and one colour
       // component of each right-hand side live at a time (register budget)
@@ -497,6 +497,8 @@ template int launch_ru_convert_dot_df<32>(void*, DfField, const void*, int, RedS
 template int launch_ru_convert_dot_df<16>(void*, DfField, const void*, int, RedScratch, RedTarget, const int*,
                                           cudaStream_t);
 template int launch_ru_convert_dot_df<15>(void*, DfField, const void*, int, RedScratch, RedTarget, const int*,
+                                          cudaStream_t);
+template int launch_ru_convert_dot_df<31>(void*, DfField, const void*, int, RedScratch, RedTarget, const int*,
                                           cudaStream_t);
 template int launch_convert_from_df<32>(void*, DfField, int, cudaStream_t);
 template int launch_convert_from_df<64>(void*, DfField, int, cudaStream_t);

@@ -25,6 +25,7 @@ template <int P> struct DslashArgs {
   const uint4* links;  // this parity's 16-byte chunks, [chunk][site]
   float fat_scale, long_scale;  // long_scale = c3/2 for two-row storage
   Spinor<P> in;
+  int s_begin, s_end;  // output sites computed: [s_begin, s_end) (all: 0, Vh)
 };
 
 // The complex number k of a group of link chunks held in registers (k is a
@@ -37,6 +38,7 @@ __device__ __forceinline__ typename Prec<P>::A2 cget(const uint4 (&buf)[NCH], in
 template <int NCH>
 __device__ __forceinline__ void load_chunks(uint4 (&buf)[NCH], const uint4* __restrict__ L, int c0, int n, int Vh,
                                             int s) {
+  s = STAG_BOUND(s, Vh, BOUND_LINK);
 #pragma unroll
   for (int j = 0; j < NCH; ++j)
     if (j < n) buf[j] = __ldg(L + (size_t)(c0 + j) * Vh + s);
@@ -72,7 +74,7 @@ __device__ __forceinline__ void hop_recon12(A2 acc[3], const uint4 (&buf)[NCH], 
     cmac(t[1], m[3 + j], psi[j]);
     cmac(t[2], r2, psi[j]);
   }
-  if (P == 15) {
+  if (fixed_links(P)) {
     // rows hold integers 32767 * entry: row 2 (and so t[2]) comes out 32767 times too large
     t[2].x *= 1.0f / FX_ONE;
     t[2].y *= 1.0f / FX_ONE;
@@ -149,7 +151,7 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<P>& a, int s, typen
       SpinorLoad<P>::ld(a.in, cb_neighbour(g, s, c, mu, -3), psi);
       hop_full<P>(accL, buf, 0, psi);
     }
-  } else if constexpr (P == 32) {
+  } else if constexpr (Chunk<P>::PER == 2) {
     constexpr int NCH = CPM / 2;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
@@ -185,8 +187,8 @@ __host__ __device__ constexpr int shape_minb(int v) { return v == 1 ? 4 : v == 3
 template <int P, int NL, int B, int MINB>
 __global__ void __launch_bounds__(B, MINB) k_dslash(DslashArgs<P> a, Spinor<P> out, const int* flags) {
   if (stopped(flags)) return;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.g.Vh) return;
+  int s = a.s_begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.s_end) return;
   typename Prec<P>::A2 d[3];
   dslash_site<P, NL>(a, s, d);
   SpinorLoad<P>::st(out, s, d);
@@ -201,9 +203,9 @@ __global__ void __launch_bounds__(B, MINB)
   using A2 = typename Prec<P>::A2;
   using A = typename Prec<P>::A;
   if (stopped(flags)) return;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int s = a.s_begin + blockIdx.x * blockDim.x + threadIdx.x;
   double red[1] = {0.0};
-  if (s < a.g.Vh) {
+  if (s < a.s_end) {
     prefetch_spinor_l2<P>(x, s);  // read by the epilogue, after the stencil
     A2 d[3], xv[3], o[3];
     dslash_site<P, NL>(a, s, d);
@@ -245,16 +247,18 @@ static DslashArgs<P> make_args(const stag_lattice_s* lat, Spinor<P> in, int out_
   a.g = lat->g;
   a.out_parity = out_parity;
   a.links = (const uint4*)((const char*)L.data + (size_t)out_parity * L.parity_stride);
-  const double fx = P == 15 ? 1.0 / 32767.0 : 1.0;  // fixed point: integers -> entries
+  const double fx = fixed_links(P) ? 1.0 / 32767.0 : 1.0;  // fixed point: integers -> entries
   a.fat_scale = (float)(L.fat_scale * fx);
   a.long_scale = (float)((L.nl == 6 ? 0.5 * lat->c3 : (double)L.long_scale) * fx);
   a.in = in;
+  a.s_begin = 0;
+  a.s_end = lat->g.Vh;
   return a;
 }
 
 template <int P, int NL>
 static void dispatch_plain(int shape, const DslashArgs<P>& a, Spinor<P> out, const int* flags, cudaStream_t st) {
-  const int Vh = a.g.Vh;
+  const int Vh = a.s_end - a.s_begin;
 #define STAG_PL(V)                                                                                \
   k_dslash<P, NL, shape_block(V), shape_minb(V)>                                                  \
       <<<(Vh + shape_block(V) - 1) / shape_block(V), shape_block(V), 0, st>>>(a, out, flags)
@@ -271,7 +275,7 @@ template <int P, int NL, int RED>
 static void dispatch_epi(int shape, const DslashArgs<P>& a, Spinor<Acc<P>::value> out, Spinor<P> x, double ax,
                          Spinor<Acc<P>::value> y, double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags,
                          cudaStream_t st) {
-  const int Vh = a.g.Vh;
+  const int Vh = a.s_end - a.s_begin;
 #define STAG_EP(V)                                                                                \
   k_dslash_epi<P, NL, RED, shape_block(V), shape_minb(V)>                                         \
       <<<(Vh + shape_block(V) - 1) / shape_block(V), shape_block(V), 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags)
@@ -286,9 +290,13 @@ static void dispatch_epi(int shape, const DslashArgs<P>& a, Spinor<Acc<P>::value
 
 template <int P>
 static int plain_with_shape(const stag_lattice_s* lat, int shape, Spinor<P> out, Spinor<P> in, int out_parity,
-                            const int* flags, cudaStream_t st) {
+                            const int* flags, cudaStream_t st, int s0 = 0, int s1 = -1) {
   const LinkCopy& L = lat->links[prec_index<P>()];
   DslashArgs<P> a = make_args<P>(lat, in, out_parity);
+  if (s1 >= 0) {
+    a.s_begin = s0;
+    a.s_end = s1;
+  }
   constexpr int NL2 = P == 64 ? 9 : 6;
   if (P == 64 || L.nl == 9)
     dispatch_plain<P, 9>(shape, a, out, flags, st);
@@ -300,10 +308,15 @@ static int plain_with_shape(const stag_lattice_s* lat, int shape, Spinor<P> out,
 template <int P>
 static int epi_with_shape(const stag_lattice_s* lat, int shape, Spinor<Acc<P>::value> out, Spinor<P> in,
                           int out_parity, Spinor<P> x, double ax, Spinor<Acc<P>::value> y, double ay, double ad,
-                          int red, RedScratch rs, RedTarget tgt, const int* flags, cudaStream_t st) {
+                          int red, RedScratch rs, RedTarget tgt, const int* flags, cudaStream_t st, int s0 = 0,
+                          int s1 = -1) {
   const LinkCopy& L = lat->links[prec_index<P>()];
   DslashArgs<P> a = make_args<P>(lat, in, out_parity);
-  const int G = (lat->g.Vh + shape_block(shape) - 1) / shape_block(shape);
+  if (s1 >= 0) {
+    a.s_begin = s0;
+    a.s_end = s1;
+  }
+  const int G = (a.s_end - a.s_begin + shape_block(shape) - 1) / shape_block(shape);
   if (red && G > rs.max_grid) return STAG_EINVAL;
   RedBuf rb{rs.partials, rs.counter};
   constexpr int NL2 = P == 64 ? 9 : 6;
@@ -339,6 +352,28 @@ int launch_dslash_epi(const stag_lattice_s* lat, Spinor<Acc<P>::value> out, Spin
   if (!L.present) return STAG_EINVAL;
   ProfScope ps(P == 64 ? "dslash64_epi" : "dslash_epi", st);
   return epi_with_shape<P>(lat, L.shape_epi, out, in, out_parity, x, ax, y, ay, ad, red, rs, tgt, flags, st);
+}
+
+// The same two kernels on the output sites [s0, s1) only (the interior of a
+// rank's slab in the domain-decomposed operator, dd.cu).
+template <int P>
+int launch_dslash_range(const stag_lattice_s* lat, Spinor<P> out, Spinor<P> in, int out_parity, int s0, int s1,
+                        const int* flags, cudaStream_t st) {
+  const LinkCopy& L = lat->links[prec_index<P>()];
+  if (!L.present || s0 < 0 || s1 > lat->g.Vh || s1 <= s0) return STAG_EINVAL;
+  ProfScope ps(P == 64 ? "dslash64" : "dslash", st);
+  return plain_with_shape<P>(lat, L.shape_plain, out, in, out_parity, flags, st, s0, s1);
+}
+
+template <int P>
+int launch_dslash_epi_range(const stag_lattice_s* lat, Spinor<Acc<P>::value> out, Spinor<P> in, int out_parity,
+                            Spinor<P> x, double ax, Spinor<Acc<P>::value> y, double ay, double ad, int red,
+                            RedScratch rs, RedTarget tgt, int s0, int s1, const int* flags, cudaStream_t st) {
+  const LinkCopy& L = lat->links[prec_index<P>()];
+  if (!L.present || s0 < 0 || s1 > lat->g.Vh || s1 <= s0) return STAG_EINVAL;
+  ProfScope ps(P == 64 ? "dslash64_epi" : "dslash_epi", st);
+  return epi_with_shape<P>(lat, L.shape_epi, out, in, out_parity, x, ax, y, ay, ad, red, rs, tgt, flags, st, s0,
+                           s1);
 }
 
 // Autotuner: times every launch shape of the plain and the fused-epilogue
@@ -406,6 +441,11 @@ int tune_dslash(stag_lattice_s* lat, cudaStream_t st) {
   template int launch_dslash_epi<P>(const stag_lattice_s*, Spinor<Acc<P>::value>, Spinor<P>, int, Spinor<P>, \
                                     double, Spinor<Acc<P>::value>, double, double, int, RedScratch, RedTarget, \
                                     const int*, cudaStream_t);                                              \
-  template int tune_dslash<P>(stag_lattice_s*, cudaStream_t);
+  template int tune_dslash<P>(stag_lattice_s*, cudaStream_t);                                                  \
+  template int launch_dslash_range<P>(const stag_lattice_s*, Spinor<P>, Spinor<P>, int, int, int, const int*,    \
+                                      cudaStream_t);                                                             \
+  template int launch_dslash_epi_range<P>(const stag_lattice_s*, Spinor<Acc<P>::value>, Spinor<P>, int, Spinor<P>, \
+                                          double, Spinor<Acc<P>::value>, double, double, int, RedScratch,          \
+                                          RedTarget, int, int, const int*, cudaStream_t);
 
 }  // namespace stag

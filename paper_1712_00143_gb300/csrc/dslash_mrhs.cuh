@@ -71,6 +71,7 @@ template <int P, int NE, int NCMAX>
 __device__ __forceinline__ int load_hop(uint4 (&b)[NCMAX], const uint4* __restrict__ L, int k0, int Vh, int s) {
   constexpr int PER = Chunk<P>::PER;
   const int c0 = k0 / PER, c1 = (k0 + NE - 1) / PER;
+  s = STAG_BOUND(s, Vh, BOUND_LINK);
 #pragma unroll
   for (int j = 0; j < NCMAX; ++j)
     if (c0 + j <= c1) b[j] = __ldg(L + (size_t)(c0 + j) * Vh + s);
@@ -112,7 +113,7 @@ __device__ __forceinline__ void hop_recon12_m(A2 (&acc)[N][3], const uint4 (&buf
     A2 r2;
     r2.x = m[k].x * m[3 + l].x - m[k].y * m[3 + l].y - (m[l].x * m[3 + k].x - m[l].y * m[3 + k].y);
     r2.y = -(m[k].x * m[3 + l].y + m[k].y * m[3 + l].x - (m[l].x * m[3 + k].y + m[l].y * m[3 + k].x));
-    if (P == 15) {
+    if (fixed_links(P)) {
       r2.x *= 1.0f / FX_ONE;
       r2.y *= 1.0f / FX_ONE;
     }

@@ -53,7 +53,7 @@ struct stag_lattice_s {
   struct MrhsTune {
     int variant = -1;
     float us = 0.f;
-  } mrhs[5][4];
+  } mrhs[6][4];  // by the ABI precision (stag_prec), tuned per format
   stag::LinkCopy links[5];  // by stag_prec (STAG_DF64 = 4: FP64 split into hi + lo floats)
   stag::Workspace ws;
 };
@@ -114,8 +114,17 @@ int build_link_copy(stag_lattice_s* lat, int prec, int recon, const double2* fat
 
 // ------------------------------------------------------------------- dslash
 // Storage format P of the links and spinors (64, 32, 16 = binary16, 15 =
-// 16-bit fixed point); accumulation precision PA = 64 for P = 64, else 32.
+// 16-bit fixed point, 31 = 16-bit fixed-point links with FP32 vectors);
+// accumulation precision PA = 64 for P = 64, else 32.
 template <int P> struct Acc { static constexpr int value = (P == 64) ? 64 : 32; };
+// The link copy an operator precision of the ABI reads (STAG_FX16L32 reads
+// the 16-bit fixed-point copy).
+inline int link_copy_of(int prec) { return prec == STAG_FX16L32 ? STAG_FX16 : prec; }
+// The ABI precision (stag_prec) of a format tag.
+template <int P> constexpr int abi_prec() {
+  return P == 64 ? STAG_FP64 : P == 32 ? STAG_FP32 : P == 16 ? STAG_FP16 : P == 31 ? STAG_FX16L32 : STAG_FX16;
+}
+// The link copy a format reads (tag 31 reads the 16-bit fixed-point copy).
 template <int P> constexpr int prec_index() {
   return P == 64 ? STAG_FP64 : P == 32 ? STAG_FP32 : P == 16 ? STAG_FP16 : STAG_FX16;
 }
@@ -133,6 +142,16 @@ template <int P>
 int launch_dslash_epi(const stag_lattice_s* lat, Spinor<Acc<P>::value> out, Spinor<P> in, int out_parity,
                       Spinor<P> x, double ax, Spinor<Acc<P>::value> y, double ay, double ad, int red,
                       RedScratch rs, RedTarget tgt, const int* flags, cudaStream_t st);
+
+// The plain and the fused-epilogue kernel on the output sites [s0, s1) only
+// (flags: a solver's stop word, or null).
+template <int P>
+int launch_dslash_range(const stag_lattice_s* lat, Spinor<P> out, Spinor<P> in, int out_parity, int s0, int s1,
+                        const int* flags, cudaStream_t st);
+template <int P>
+int launch_dslash_epi_range(const stag_lattice_s* lat, Spinor<Acc<P>::value> out, Spinor<P> in, int out_parity,
+                            Spinor<P> x, double ax, Spinor<Acc<P>::value> y, double ay, double ad, int red,
+                            RedScratch rs, RedTarget tgt, int s0, int s1, const int* flags, cudaStream_t st);
 
 // ------------------------------------------------------------------- blas
 // canonical [Vh][3] complex double <-> internal Spinor<P>

@@ -12,10 +12,11 @@ using namespace stag;
 
 extern "C" int stag_tuned_mrhs(stag_lattice_t lat, int prec, int nrhs, int* threads_per_site, int* min_blocks,
                                double* us) {
-  if (!lat || prec < 0 || prec > 3 || !lat->links[prec].present) return STAG_EINVAL;
+  if (!lat || prec < 0 || prec > STAG_FX16L32 || prec == STAG_DF64 || !lat->links[link_copy_of(prec)].present)
+    return STAG_EINVAL;
   if (nrhs != 2 && nrhs != 4 && nrhs != 8) return STAG_EINVAL;
   const auto& slot = lat->mrhs[prec][mrhs_nindex(nrhs)];
-  const int p = prec == STAG_FP64 ? 64 : prec == STAG_FP32 ? 32 : prec == STAG_FP16 ? 16 : 15;
+  const int p = prec == STAG_FP64 ? 64 : prec == STAG_FP32 ? 32 : prec == STAG_FP16 ? 16 : prec == STAG_FX16L32 ? 31 : 15;
   const int v = slot.variant >= 0 ? slot.variant : mrhs_default_variant(p, nrhs);
   if (threads_per_site) *threads_per_site = mvariant(v).sp;
   if (min_blocks) *min_blocks = mvariant(v).minb;

@@ -1,7 +1,7 @@
 // mrhs_kernels.cuh -- the N-right-hand-side Dslash kernels (plain, and with
 // the fused axpy and per-system FP64 reductions), their launch variants and
 // the autotuner that picks among them.  Instantiated per storage format in
-// mrhs64.cu, mrhs32.cu, mrhs16.cu and mrhs15.cu.
+// mrhs64.cu, mrhs32.cu, mrhs31.cu, mrhs16.cu and mrhs15.cu.
 //
 // Launch variants.  A block has MB = 128 threads.  SP threads share a site,
 // each taking N / SP of the group's right-hand sides (the link chunks that
@@ -36,17 +36,19 @@ constexpr int kNumMVariants = 6;
 // The variant used without tuning: FP32 with up to four right-hand sides
 // fits in 80 registers without spilling (six blocks, 24 warps, measured
 // faster than five); the other forms take no cap.
-__host__ __device__ constexpr int mrhs_default_variant(int p, int n) { return (p == 32 && n <= 4) ? 1 : 0; }
+__host__ __device__ constexpr int mrhs_default_variant(int p, int n) {
+  return ((p == 32 || p == 31) && n <= 4) ? 1 : 0;
+}
 
 // Variants compiled for (format, Naik storage, N): the default always; the
-// tuned set for two-row Naik storage in FP32 (N = 2, 4, 8; the 80-register
+// tuned set for two-row Naik storage with FP32 vectors (N = 2, 4, 8; the 80-register
 // cap only for at most four right-hand sides per thread, beyond which it
 // spills) and the 16-bit formats (N = 2, 4, the groups the batched solver
 // forms for them; their decode needs more than 80 registers).
 __host__ __device__ constexpr bool mrhs_variant_built(int p, int nl, int n, int v) {
   return v == mrhs_default_variant(p, n) ||
          (nl == 6 && n % mvariant(v).sp == 0 &&
-          ((p == 32 && (mvariant(v).minb != 6 || n / mvariant(v).sp <= 4)) ||
+          (((p == 32 || p == 31) && (mvariant(v).minb != 6 || n / mvariant(v).sp <= 4)) ||
            ((p == 16 || p == 15) && n <= 4 && mvariant(v).minb != 6)));
 }
 
@@ -139,7 +141,7 @@ template <int P> DslashArgsM<P> make_args_m(const stag_lattice_s* lat, SpinorM<P
   a.g = lat->g;
   a.out_parity = out_parity;
   a.links = (const uint4*)((const char*)L.data + (size_t)out_parity * L.parity_stride);
-  const double fx = P == 15 ? 1.0 / 32767.0 : 1.0;
+  const double fx = fixed_links(P) ? 1.0 / 32767.0 : 1.0;
   a.fat_scale = (float)(L.fat_scale * fx);
   a.long_scale = (float)((L.nl == 6 ? 0.5 * lat->c3 : (double)L.long_scale) * fx);
   a.in = in;
@@ -150,7 +152,7 @@ __host__ __device__ constexpr int mrhs_nindex(int n) { return n == 2 ? 0 : n == 
 
 // The variant a group of N right-hand sides of format P runs with on this lattice.
 template <int P, int N> int mrhs_variant(const stag_lattice_s* lat) {
-  const int v = lat->mrhs[prec_index<P>()][mrhs_nindex(N)].variant;
+  const int v = lat->mrhs[abi_prec<P>()][mrhs_nindex(N)].variant;
   return v >= 0 ? v : mrhs_default_variant(P, N);
 }
 
@@ -259,7 +261,7 @@ int mdslash_epi(const stag_lattice_s* lat, SpinorM<Acc<P>::value> out, SpinorM<P
 // in the process-wide cache under the key (kernel, format, Naik storage, N,
 // extents).  Must not run while a stream is being captured.
 template <int P, int N> int tune_mrhs(stag_lattice_s* lat, cudaStream_t st) {
-  auto& slot = lat->mrhs[prec_index<P>()][mrhs_nindex(N)];
+  auto& slot = lat->mrhs[abi_prec<P>()][mrhs_nindex(N)];
   if (slot.variant >= 0) return STAG_OK;
   const LinkCopy& L = lat->links[prec_index<P>()];
   if (!L.present) return STAG_EINVAL;
@@ -268,7 +270,7 @@ template <int P, int N> int tune_mrhs(stag_lattice_s* lat, cudaStream_t st) {
     slot.variant = def;
     return STAG_OK;
   }
-  const std::string key = tune_key("dslash_mrhs", prec_index<P>(), L.nl, N, lat->dims);
+  const std::string key = tune_key("dslash_mrhs", abi_prec<P>(), L.nl, N, lat->dims);
   int cached = -1;
   double cached_us = 0.0;
   if (tune_cache_get(key, &cached, &cached_us) && cached >= 0 && cached < kNumMVariants &&

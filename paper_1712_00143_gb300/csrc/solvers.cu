@@ -400,14 +400,16 @@ int learned_solve(stag_lattice_s* lat, double2* x, const double2* b, double mass
 
 static int check_params(const stag_solve_params* p) {
   if (!p) return STAG_EINVAL;
-  if (!(p->tol > 0.0) || p->max_iter < 0 || p->mode < 0 || p->mode > 4) return STAG_EINVAL;
+  if (!(p->tol > 0.0) || p->max_iter < 0 || p->mode < 0 || p->mode > STAG_MIXED16L) return STAG_EINVAL;
   if (p->mode == STAG_LEARNED && !p->precond) return STAG_EINVAL;
   if (p->mode != STAG_PLAIN64 && !(p->delta > 0.0 && p->delta < 1.0)) return STAG_EINVAL;
   return STAG_OK;
 }
 
+// the link copy a mode's Krylov loop reads
 static int mode_prec(int mode) {
-  return mode == STAG_PLAIN64 ? STAG_FP64 : mode == STAG_MIXED16 ? STAG_FP16 : mode == STAG_MIXEDFX16 ? STAG_FX16 : STAG_FP32;
+  return mode == STAG_PLAIN64 ? STAG_FP64 : mode == STAG_MIXED16 ? STAG_FP16
+       : (mode == STAG_MIXEDFX16 || mode == STAG_MIXED16L) ? STAG_FX16 : STAG_FP32;
 }
 
 extern "C" {
@@ -429,6 +431,7 @@ int stag_cg(stag_lattice_t lat, void* x, const void* b, double mass, const stag_
     case STAG_PLAIN64: return cg_solve<64>(lat, (double2*)x, (const double2*)b, shift, prm, info, st);
     case STAG_MIXED32: return cg_solve<32>(lat, (double2*)x, (const double2*)b, shift, prm, info, st);
     case STAG_MIXED16: return cg_solve<16>(lat, (double2*)x, (const double2*)b, shift, prm, info, st);
+    case STAG_MIXED16L: return cg_solve<31>(lat, (double2*)x, (const double2*)b, shift, prm, info, st);
     default: return cg_solve<15>(lat, (double2*)x, (const double2*)b, shift, prm, info, st);
   }
 }
@@ -451,6 +454,7 @@ int stag_multishift_cg(stag_lattice_t lat, void* const* x, const void* b, double
     case STAG_PLAIN64: return ms_solve<64>(lat, xs, (const double2*)b, mass, shifts, nshift, prm, infos, st);
     case STAG_MIXED32: return ms_solve<32>(lat, xs, (const double2*)b, mass, shifts, nshift, prm, infos, st);
     case STAG_MIXED16: return ms_solve<16>(lat, xs, (const double2*)b, mass, shifts, nshift, prm, infos, st);
+    case STAG_MIXED16L: return ms_solve<31>(lat, xs, (const double2*)b, mass, shifts, nshift, prm, infos, st);
     default: return ms_solve<15>(lat, xs, (const double2*)b, mass, shifts, nshift, prm, infos, st);
   }
 }

@@ -39,6 +39,7 @@ const char* prec_name(int prec) {
     case STAG_FP16: return "fp16";
     case STAG_FX16: return "fx16";
     case STAG_DF64: return "df64";
+    case STAG_FX16L32: return "fx16l";
     default: return "p?";
   }
 }

@@ -21,7 +21,7 @@ def _stag():
     return stag
 
 
-@pytest.mark.parametrize("mode", ["plain64", "mixed32", "mixedfx16", "mixed16"])
+@pytest.mark.parametrize("mode", ["plain64", "mixed32", "mixedfx16", "mixed16", "mixed16l"])
 def test_batch_small_two_lattices(mode):
     stag = _stag()
     specs = [((8, 8, 8, 8), 0.1, 3, 1000), ((4, 6, 8, 10), 0.05, 8, 1001), ((4, 4, 4, 6), 0.2, 1, 1002)]

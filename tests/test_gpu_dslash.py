@@ -100,13 +100,14 @@ def test_free_field_through_gpu():
     h.free()
 
 
-@pytest.mark.parametrize("prec,recon", [("fp64", 18), ("fp32", 12), ("fp16", 12), ("fx16", 12), ("fp32", 18), ("fx16", 18)])
+@pytest.mark.parametrize("prec,recon", [("fp64", 18), ("fp32", 12), ("fp16", 12), ("fx16", 12), ("fp32", 18), ("fx16", 18),
+                                        ("fx16l", 12)])
 def test_dslash_32_4_sampled_sites(prec, recon):
     """Full-size 32^4 workload: sampled output sites vs the oracle site by site."""
     stag = _stag()
     dims = (32, 32, 32, 32)
     f = Field.get(dims)
-    h = f.handle(recon=recon, prec_mask=(1 << stag.PREC[prec]))
+    h = f.handle(recon=recon, prec_mask=(1 << stag.PREC["fx16" if prec == "fx16l" else prec]))
     psi = synth.random_spinor(dims, 41)
     pd = dev(psi)
     out = torch.empty_like(pd)

@@ -20,7 +20,7 @@ def _stag():
     return stag
 
 
-@pytest.mark.parametrize("mode", ["plain64", "mixed32", "mixed16", "mixedfx16"])
+@pytest.mark.parametrize("mode", ["plain64", "mixed32", "mixed16", "mixedfx16", "mixed16l"])
 @pytest.mark.parametrize("recon", [18, 12])
 def test_cg_8_4(mode, recon):
     """8^4, m = 0.1, Gaussian even source: the small single-mass workload."""
