@@ -153,6 +153,7 @@ template <int P, int N> struct Group : GroupBase {
   // the anchor (ya64, its residual radf; see McgState), y - ya, the odd
   // intermediate and the residual
   bool use_df = false;
+  float2* pw = nullptr;  // per-warp partials of <p, Ap> (FP32-arithmetic formats)
   SpinorM<64> ya64;
   DfField radf, ydf, tdf, rdf;
   RedScratch rs;
@@ -183,6 +184,7 @@ template <int P, int N> struct Group : GroupBase {
     }
     t64 = ws_spinorm<64>(lat, pre + "t64", N, &s);
     r64 = ws_spinorm<64>(lat, pre + "r64", N, &s);
+    pw = (float2*)lat->ws.get(pre + "pw", sizeof(float2) * N * ((size_t)Vh / 32 + 4), &s);
     dst = (McgState*)lat->ws.get(pre + "state", sizeof(McgState), &s);
     dscal = (double*)lat->ws.get(pre + "scal", sizeof(double) * 2 * MAX_RHS, &s);
     if (s) return s;
@@ -301,17 +303,7 @@ template <int P, int N> struct Group : GroupBase {
         TRYB(last_launch_status());
       }
       TRYB((mdslash<P, N>(lat, t, p, 1, flags, st)));
-      // Ap = shift p - D_eo t without a reduction in the operator kernel, then
-      // <p, Ap> per system in a pass of its own: measured faster than the
-      // fused form, whose per-block reductions hold every block of the
-      // operator grid (4096 at 32^4) until its slowest warp is done
-      TRYB((mdslash_epi<P, N, 0>(lat, Ap, t, 0, p, shift, none, 0.0, -1.0, rs, RedTarget{RED_STORE, nullptr, nullptr},
-                                 flags, st)));
-      {
-        ProfScope ps("reduce", st);
-        k_mcg_pap<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(p, Ap, dst, RedBuf{rs.partials, rs.counter});
-      }
-      TRYB(last_launch_status());
+      TRYB(operator_epilogue(none, flags));
       {
         ProfScope ps("blas", st);
         k_mcg_update<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(xh, rh, p, Ap, dst,
@@ -321,6 +313,27 @@ template <int P, int N> struct Group : GroupBase {
       pending_p = true;
     }
     return STAG_OK;
+  }
+
+  // Ap = shift p - D_eo t and <p_r, Ap_r> -> alpha_r.  FP32-arithmetic
+  // formats: the operator kernel leaves per-warp double-float partials of
+  // <p, Ap> (no block barrier, no extra pass) and one small block sums them;
+  // FP64: the operator without a reduction, then <p, Ap> in a level-1 pass
+  // (a block-tree reduction fused into the operator grid, 4096 blocks at
+  // 32^4, held every block until its slowest warp was done: measured slower)
+  int operator_epilogue(SpinorM<PV> none, const int* flags) {
+    const int Vh = lat->g.Vh;
+    if constexpr (P != 64) {
+      TRYB((mdslash_epi<P, N, 3>(lat, Ap, t, 0, p, shift, none, 0.0, -1.0, RedScratch{(double*)pw, nullptr, 0},
+                                 RedTarget{RED_STORE, nullptr, nullptr}, flags, st)));
+      return launch_mcg_alpha_pw<P, N>(lat, pw, dst, st);
+    } else {
+      TRYB((mdslash_epi<P, N, 0>(lat, Ap, t, 0, p, shift, none, 0.0, -1.0, rs, RedTarget{RED_STORE, nullptr, nullptr},
+                                 flags, st)));
+      ProfScope ps("reduce", st);
+      k_mcg_pap<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(p, Ap, dst, RedBuf{rs.partials, rs.counter});
+      return last_launch_status();
+    }
   }
 
   // Host-driven update: double-float, or the FP64 update that moves the
@@ -407,13 +420,7 @@ template <int P, int N> struct Group : GroupBase {
       k_mcg_clear_skip<<<1, 1, 0, st>>>(dst);
       TRYB(last_launch_status());
       TRYB((mdslash<P, N>(lat, t, p, 1, flags, st)));
-      TRYB((mdslash_epi<P, N, 0>(lat, Ap, t, 0, p, shift, none, 0.0, -1.0, rs, RedTarget{RED_STORE, nullptr, nullptr},
-                                 flags, st)));
-      {
-        ProfScope ps("reduce", st);
-        k_mcg_pap<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(p, Ap, dst, RedBuf{rs.partials, rs.counter});
-      }
-      TRYB(last_launch_status());
+      TRYB(operator_epilogue(none, flags));
       {
         ProfScope ps("blas", st);
         k_mcg_update<P, N><<<grid_red(Vh, rs.max_grid), 256, 0, st>>>(xh, rh, p, Ap, dst,

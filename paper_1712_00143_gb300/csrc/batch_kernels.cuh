@@ -47,10 +47,7 @@ __global__ void __launch_bounds__(256) k_mcg_update(SpinorM<Acc<P>::value> xh, S
       SpinorLoadM<PV>::st(rh, s, r, rv);
     }
   }
-  double red[N];
-#pragma unroll
-  for (int r = 0; r < N; ++r) red[r] = acc[r].value();
-  grid_reduce<N>(red, rb, RedTarget{RED_MCG_BETA, g, nullptr});
+  grid_reduce_acc<N>(acc, rb, RedTarget{RED_MCG_BETA, g, nullptr});
 }
 
 // Re<p_r, Ap_r> -> alpha_r (RED_MCG_ALPHA): the CG dot product read back
@@ -76,10 +73,7 @@ __global__ void __launch_bounds__(256) k_mcg_pap(SpinorM<P> p, SpinorM<Acc<P>::v
       }
     }
   }
-  double red[N];
-#pragma unroll
-  for (int r = 0; r < N; ++r) red[r] = acc[r].value();
-  grid_reduce<N>(red, rb, RedTarget{RED_MCG_ALPHA, g, nullptr});
+  grid_reduce_acc<N>(acc, rb, RedTarget{RED_MCG_ALPHA, g, nullptr});
 }
 
 // p_r = rh_r + beta_r p_r
@@ -165,13 +159,13 @@ __global__ void k_mru_convert_dot(SpinorM<Acc<P>::value> rh, SpinorM<64> r64, Sp
       }
     }
   }
-  double red[2 * N];
+  Acc1<A> all[2 * N];
 #pragma unroll
   for (int r = 0; r < N; ++r) {
-    red[2 * r] = re[r].value();
-    red[2 * r + 1] = im[r].value();
+    all[2 * r] = re[r];
+    all[2 * r + 1] = im[r];
   }
-  grid_reduce<2 * N>(red, rb, RedTarget{RED_MCG_RU_ORTHO, g, nullptr});
+  grid_reduce_acc<2 * N>(all, rb, RedTarget{RED_MCG_RU_ORTHO, g, nullptr});
 }
 
 // p_r = rh_r + beta_r (p_r - c_r rh_r)
@@ -273,10 +267,7 @@ template <int P, int N> __global__ void k_mnorm2(SpinorM<P> v, RedBuf rb, RedTar
       }
     }
   }
-  double red[N];
-#pragma unroll
-  for (int r = 0; r < N; ++r) red[r] = acc[r].value();
-  grid_reduce<N>(red, rb, tgt);
+  grid_reduce_acc<N>(acc, rb, tgt);
 }
 
 #undef MGRID

@@ -128,8 +128,8 @@ template <int P> __global__ void k_norm2(Spinor<P> v, RedBuf rb, RedTarget tgt) 
       acc.add_prod(a[c].y, a[c].y);
     }
   }
-  double r[1] = {acc.value()};
-  grid_reduce<1>(r, rb, tgt);
+  Acc1<A> tot[1] = {acc};
+  grid_reduce_acc<1>(tot, rb, tgt);
 }
 
 template <int P> int launch_norm2(Spinor<P> v, RedScratch rs, RedTarget tgt, cudaStream_t st) {
@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(BB) k_cg_update(Spinor<PV> xh, Spinor<PV> rh, 
   GRID_STRIDE2(xh.Vh, CGU2, CGU1)
 #undef CGU2
 #undef CGU1
-  double r[1] = {acc.value()};
-  grid_reduce<1>(r, rb, RedTarget{RED_CG_BETA, st, nullptr});
+  Acc1<A> tot[1] = {acc};
+  grid_reduce_acc<1>(tot, rb, RedTarget{RED_CG_BETA, st, nullptr});
 }
 
 template <int P>
@@ -287,8 +287,8 @@ __global__ void k_ru_convert_dot(Spinor<PV> rh, Spinor<64> r, Spinor<P> p, CgSta
       im.add_prod(-o[c].y, (A)pv[c].x);
     }
   }
-  double acc[2] = {re.value(), im.value()};
-  grid_reduce<2>(acc, rb, RedTarget{RED_RU_ORTHO, st, nullptr});
+  Acc1<A> tot[2] = {re, im};
+  grid_reduce_acc<2>(tot, rb, RedTarget{RED_RU_ORTHO, st, nullptr});
 }
 
 template <int P>
@@ -362,8 +362,8 @@ __global__ void __launch_bounds__(BB) k_ms_r_update(Spinor<PV> r, Spinor<PV> Ap,
   GRID_STRIDE2(r.Vh, MSR2, MSR1)
 #undef MSR2
 #undef MSR1
-  double red[1] = {acc.value()};
-  grid_reduce<1>(red, rb, RedTarget{RED_MS_BETA, ms, nullptr});
+  Acc1<A> tot[1] = {acc};
+  grid_reduce_acc<1>(tot, rb, RedTarget{RED_MS_BETA, ms, nullptr});
 }
 
 template <int P>

@@ -792,6 +792,109 @@ template <int NV> __device__ __forceinline__ void grid_reduce(double (&v)[NV], R
   }
 }
 
+// ---- the same sums in double-float: GB300's FP64 pipe is so narrow (about
+// 1.75 results per clock per SM) that even the FP64 additions of a block
+// tree are visible in a memory-bound kernel, so the FP32-arithmetic kernels
+// keep their per-thread (hi, lo) sums and add them across threads and
+// blocks with TwoSum on the FP32 pipes; only the final totals become
+// doubles.  Same fixed order as the FP64 tree (deterministic).
+
+// a += b, both double-float
+__device__ __forceinline__ void df_add_df(DF& a, const DF& b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fadd_rn(s, -a.hi);
+  const float err = __fadd_rn(__fadd_rn(a.hi, -__fadd_rn(s, -v)), __fadd_rn(b.hi, -v));
+  a.hi = s;
+  a.lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
+}
+
+template <int NV> __device__ __forceinline__ void warp_sum_df(DF (&v)[NV]) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      DF w;
+      w.hi = __shfl_xor_sync(0xffffffffu, v[i].hi, o);
+      w.lo = __shfl_xor_sync(0xffffffffu, v[i].lo, o);
+      df_add_df(v[i], w);
+    }
+}
+
+// Deterministic block sum of NV double-float values; valid in thread 0.
+template <int NV> __device__ __forceinline__ void block_sum_df(DF (&v)[NV]) {
+  __shared__ float2 sm[NV][32];
+  warp_sum_df<NV>(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sm[i][w] = make_float2(v[i].hi, v[i].lo);
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (w == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const float2 q = l < nw ? sm[i][l] : make_float2(0.f, 0.f);
+      v[i].hi = q.x;
+      v[i].lo = q.y;
+    }
+    warp_sum_df<NV>(v);
+  }
+  __syncthreads();
+}
+
+// grid_reduce for per-thread double-float sums (the partials buffer holds
+// (hi, lo) float pairs in its 8-byte slots); the last block converts the
+// totals to double and finalises.
+template <int NV> __device__ __forceinline__ void grid_reduce_df(DF (&v)[NV], RedBuf rb, RedTarget tgt) {
+  block_sum_df<NV>(v);
+  float2* part = (float2*)rb.partials;
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) part[i * gridDim.x + blockIdx.x] = make_float2(v[i].hi, v[i].lo);
+    __threadfence();
+    unsigned t = atomicAdd(rb.counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  DF w[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) w[i] = DF{0.f, 0.f};
+#pragma unroll 8
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const float2 q = __ldcg(part + i * gridDim.x + b);
+      df_add_df(w[i], DF{q.x, q.y});
+    }
+  block_sum_df<NV>(w);
+  if (threadIdx.x == 0) {
+    double t[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) t[i] = df_value(w[i]);
+    finalize(tgt, t, NV);
+    *rb.counter = 0u;
+    __threadfence();
+  }
+}
+
+// The reduction of an array of per-thread accumulators: double-float sums
+// for FP32 arithmetic, the FP64 tree for FP64 arithmetic.
+template <int NV> __device__ __forceinline__ void grid_reduce_acc(Acc1<float> (&a)[NV], RedBuf rb, RedTarget tgt) {
+  DF v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = a[i].v;
+  grid_reduce_df<NV>(v, rb, tgt);
+}
+template <int NV> __device__ __forceinline__ void grid_reduce_acc(Acc1<double> (&a)[NV], RedBuf rb, RedTarget tgt) {
+  double v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = a[i].value();
+  grid_reduce<NV>(v, rb, tgt);
+}
+
 // Early-exit test shared by the Krylov-loop kernels.
 __device__ __forceinline__ bool stopped(const int* flags) { return flags != nullptr && (__ldcg(flags) & F_STOP); }
 

@@ -287,14 +287,14 @@ __global__ void k_ru_convert_dot_df(SpinorM<Acc<P>::value> rh, const float4* __r
       }
     }
   }
-  double red[3 * N];
+  Acc1<A> all[3 * N];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    red[k] = nn[k].value();
-    red[N + 2 * k] = re[k].value();
-    red[N + 2 * k + 1] = im[k].value();
+    all[k] = nn[k];
+    all[N + 2 * k] = re[k];
+    all[N + 2 * k + 1] = im[k];
   }
-  grid_reduce<3 * N>(red, rb, tgt);
+  grid_reduce_acc<3 * N>(all, rb, tgt);
 }
 
 // ||v_r||^2 of DF fields, FP64-class: (h + l)^2 = h^2 + 2 h l -> tgt
@@ -312,10 +312,7 @@ template <int N> __global__ void k_norm2_df(const float4* __restrict__ v, int Vh
         acc[k].v.lo = fmaf(2.f * d.y, d.w, acc[k].v.lo);
       }
   }
-  double red[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) red[k] = acc[k].value();
-  grid_reduce<N>(red, rb, tgt);
+  grid_reduce_acc<N>(acc, rb, tgt);
 }
 
 // Krylov-loop fields of n systems from DF fields (rounded to the nearest float)

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(B, MINB)
   using A = typename Prec<P>::A;
   if (stopped(flags)) return;
   int s = a.s_begin + blockIdx.x * blockDim.x + threadIdx.x;
-  double red[1] = {0.0};
+  Acc1<A> red[1];
   if (s < a.s_end) {
     prefetch_spinor_l2<P>(x, s);  // read by the epilogue, after the stencil
     A2 d[3], xv[3], o[3];
@@ -228,16 +228,14 @@ __global__ void __launch_bounds__(B, MINB)
     }
     SpinorLoad<Acc<P>::value>::st(out, s, o);
     if (RED) {
-      Acc1<A> acc;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        acc.add_prod(RED == 1 ? xv[i].x : o[i].x, o[i].x);
-        acc.add_prod(RED == 1 ? xv[i].y : o[i].y, o[i].y);
+        red[0].add_prod(RED == 1 ? xv[i].x : o[i].x, o[i].x);
+        red[0].add_prod(RED == 1 ? xv[i].y : o[i].y, o[i].y);
       }
-      red[0] = acc.value();
     }
   }
-  if (RED) grid_reduce<1>(red, rb, tgt);
+  if (RED) grid_reduce_acc<1>(red, rb, tgt);
 }
 
 template <int P>

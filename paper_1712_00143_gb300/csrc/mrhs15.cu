@@ -6,4 +6,7 @@ namespace stag {
 STAG_INSTANTIATE_MRHS_N(15, 2)
 STAG_INSTANTIATE_MRHS_N(15, 4)
 STAG_INSTANTIATE_MRHS_N(15, 8)
+STAG_INSTANTIATE_MRHS_RED3(15, 2)
+STAG_INSTANTIATE_MRHS_RED3(15, 4)
+STAG_INSTANTIATE_MRHS_RED3(15, 8)
 }  // namespace stag

@@ -6,4 +6,7 @@ namespace stag {
 STAG_INSTANTIATE_MRHS_N(16, 2)
 STAG_INSTANTIATE_MRHS_N(16, 4)
 STAG_INSTANTIATE_MRHS_N(16, 8)
+STAG_INSTANTIATE_MRHS_RED3(16, 2)
+STAG_INSTANTIATE_MRHS_RED3(16, 4)
+STAG_INSTANTIATE_MRHS_RED3(16, 8)
 }  // namespace stag

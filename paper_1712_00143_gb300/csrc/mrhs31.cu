@@ -7,4 +7,7 @@ namespace stag {
 STAG_INSTANTIATE_MRHS_N(31, 2)
 STAG_INSTANTIATE_MRHS_N(31, 4)
 STAG_INSTANTIATE_MRHS_N(31, 8)
+STAG_INSTANTIATE_MRHS_RED3(31, 2)
+STAG_INSTANTIATE_MRHS_RED3(31, 4)
+STAG_INSTANTIATE_MRHS_RED3(31, 8)
 }  // namespace stag

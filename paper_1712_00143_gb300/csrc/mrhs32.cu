@@ -6,6 +6,9 @@ namespace stag {
 STAG_INSTANTIATE_MRHS_N(32, 2)
 STAG_INSTANTIATE_MRHS_N(32, 4)
 STAG_INSTANTIATE_MRHS_N(32, 8)
+STAG_INSTANTIATE_MRHS_RED3(32, 2)
+STAG_INSTANTIATE_MRHS_RED3(32, 4)
+STAG_INSTANTIATE_MRHS_RED3(32, 8)
 }  // namespace stag
 
 using namespace stag;

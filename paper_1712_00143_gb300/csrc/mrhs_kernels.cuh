@@ -70,13 +70,16 @@ __global__ void __launch_bounds__(MB, MINB) k_dslash_mv(DslashArgsM<P> a, Spinor
 }
 
 // out_r = ax x_r + ay y_r + ad (D in)_r; RED = 1: Re<x_r, out_r>, RED = 2:
-// ||out_r||^2, one FP64 sum per system, finalised by the last block (RED
-// needs SP = 1: the block's threads hold the sums of one system each).
+// ||out_r||^2, one sum per system, finalised by the last block (needs SP = 1:
+// the block's threads hold the sums of one system each).  RED = 3:
+// Re<x_r, out_r> as per-warp double-float partials in rb.partials (float2
+// [N][W], W warps of site coverage; no block barrier, no last block), summed
+// by k_mcg_alpha_pw: the batched CG's <p, Ap> without a pass of its own.
 template <int P, int NL, int N, int RED, int SP, int MINB>
 __global__ void __launch_bounds__(MB, MINB)
     k_dslash_m_epi_v(DslashArgsM<P> a, SpinorM<Acc<P>::value> out, SpinorM<P> x, double ax,
                      SpinorM<Acc<P>::value> y, double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags) {
-  static_assert(N % SP == 0 && (RED == 0 || SP == 1), "variant");
+  static_assert(N % SP == 0 && (RED == 0 || RED == 3 || SP == 1), "variant");
   using A2 = typename Prec<P>::A2;
   using A = typename Prec<P>::A;
   constexpr int PA = Acc<P>::value;
@@ -92,9 +95,7 @@ __global__ void __launch_bounds__(MB, MINB)
     out.v = (char*)out.v + offa;
     if (y.v) y.v = (char*)y.v + offa;
   }
-  double red[NT];
-#pragma unroll
-  for (int r = 0; r < NT; ++r) red[r] = 0.0;
+  Acc1<A> red[NT];
   if (s < a.g.Vh) {
     // the epilogue's x_r are read after the stencil: start them towards L2 now
 #pragma unroll
@@ -122,17 +123,29 @@ __global__ void __launch_bounds__(MB, MINB)
       }
       SpinorLoadM<PA>::st(out, s, r, o);
       if (RED) {
-        Acc1<A> acc;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          acc.add_prod(RED == 1 ? xv[i].x : o[i].x, o[i].x);
-          acc.add_prod(RED == 1 ? xv[i].y : o[i].y, o[i].y);
+          red[r].add_prod(RED == 2 ? o[i].x : xv[i].x, o[i].x);  // RED 1 and 3: <x, out>
+          red[r].add_prod(RED == 2 ? o[i].y : xv[i].y, o[i].y);
         }
-        red[r] = acc.value();
       }
     }
   }
-  if constexpr (RED != 0) grid_reduce<N>(red, rb, tgt);
+  if constexpr (RED == 3) {
+    DF v[NT];
+#pragma unroll
+    for (int r = 0; r < NT; ++r) v[r] = red[r].v;
+    warp_sum_df<NT>(v);
+    if ((threadIdx.x & 31) == 0) {
+      const int W = gridDim.x * (SPB / 32);
+      const int w = blockIdx.x * (SPB / 32) + ((threadIdx.x - part * SPB) >> 5);
+      float2* pw = (float2*)rb.partials;
+#pragma unroll
+      for (int r = 0; r < NT; ++r) pw[(size_t)(part * NT + r) * W + w] = make_float2(v[r].hi, v[r].lo);
+    }
+  } else if constexpr (RED != 0) {
+    grid_reduce_acc<N>(red, rb, tgt);
+  }
 }
 
 template <int P> DslashArgsM<P> make_args_m(const stag_lattice_s* lat, SpinorM<P> in, int out_parity) {
@@ -183,7 +196,7 @@ template <int P, int NL, int N, int RED, int V>
 void launch_epi_v(int G, const DslashArgsM<P>& a, SpinorM<Acc<P>::value> out, SpinorM<P> x, double ax,
                   SpinorM<Acc<P>::value> y, double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags,
                   cudaStream_t st) {
-  if constexpr (mrhs_variant_built(P, NL, N, V) && (RED == 0 || mvariant(V).sp == 1)) {
+  if constexpr (mrhs_variant_built(P, NL, N, V) && (RED == 0 || RED == 3 || mvariant(V).sp == 1)) {
     constexpr MVariant mv = mvariant(V);
     k_dslash_m_epi_v<P, NL, N, RED, mv.sp, mv.minb><<<G, MB, 0, st>>>(a, out, x, ax, y, ay, ad, rb, tgt, flags);
   }
@@ -193,7 +206,8 @@ template <int P, int NL, int N, int RED>
 void dispatch_epi(int v, const DslashArgsM<P>& a, SpinorM<Acc<P>::value> out, SpinorM<P> x, double ax,
                   SpinorM<Acc<P>::value> y, double ay, double ad, RedBuf rb, RedTarget tgt, const int* flags,
                   cudaStream_t st) {
-  if (!mrhs_variant_built(P, NL, N, v) || (RED != 0 && mvariant(v).sp != 1)) v = mrhs_default_variant(P, N);
+  if (!mrhs_variant_built(P, NL, N, v) || (RED != 0 && RED != 3 && mvariant(v).sp != 1))
+    v = mrhs_default_variant(P, N);
   const int spb = MB / mvariant(v).sp;
   const int G = (a.g.Vh + spb - 1) / spb;
 #define STAG_EPV(V) launch_epi_v<P, NL, N, RED, V>(G, a, out, x, ax, y, ay, ad, rb, tgt, flags, st)
@@ -229,7 +243,7 @@ int mdslash_epi_v(const stag_lattice_s* lat, int v, SpinorM<Acc<P>::value> out, 
   const LinkCopy& L = lat->links[prec_index<P>()];
   if (!L.present) return STAG_EINVAL;
   DslashArgsM<P> a = make_args_m<P>(lat, in, out_parity);
-  if (RED && (a.g.Vh + MB - 1) / MB > rs.max_grid) return STAG_EINVAL;
+  if (RED && RED != 3 && (a.g.Vh + MB - 1) / MB > rs.max_grid) return STAG_EINVAL;
   ProfScope ps(P == 64 ? "dslash_mrhs64_epi" : "dslash_mrhs_epi", st);
   RedBuf rb{rs.partials, rs.counter};
   if (P != 64 && L.nl == 6)
@@ -328,11 +342,56 @@ template <int P, int N> int tune_mrhs(stag_lattice_s* lat, cudaStream_t st) {
   return STAG_OK;
 }
 
+// Per-warp partials of a RED = 3 launch for N right-hand sides of format P:
+// W = the warps of one part (right-hand-side share) over the grid; at most
+// Vh / 32 + 3.
+template <int P, int N> int mrhs_partial_warps(const stag_lattice_s* lat) {
+  const int spb = MB / mvariant(mrhs_variant<P, N>(lat)).sp;
+  return (lat->g.Vh + spb - 1) / spb * (spb / 32);
+}
+
+// <p_r, Ap_r> of every system from the per-warp partials of a RED = 3
+// operator launch (float2 [N][W]): one block, double-float sums in a fixed
+// order, then RED_MCG_ALPHA.  Nothing once the group's stop word is set.
+template <int N> __global__ void __launch_bounds__(512) k_mcg_alpha_pw(const float2* pw, int W, McgState* g) {
+  if (stopped(&g->flags)) return;
+  DF v[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) v[r] = DF{0.f, 0.f};
+  for (int w = threadIdx.x; w < W; w += blockDim.x)
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      const float2 q = __ldcg(pw + (size_t)r * W + w);
+      df_add_df(v[r], DF{q.x, q.y});
+    }
+  block_sum_df<N>(v);
+  if (threadIdx.x == 0) {
+    double t[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) t[r] = df_value(v[r]);
+    finalize(RedTarget{RED_MCG_ALPHA, g, nullptr}, t, N);
+  }
+}
+
+template <int P, int N>
+int launch_mcg_alpha_pw(const stag_lattice_s* lat, const float2* pw, McgState* g, cudaStream_t st) {
+  ProfScope ps("reduce", st);
+  k_mcg_alpha_pw<N><<<1, 512, 0, st>>>(pw, mrhs_partial_warps<P, N>(lat), g);
+  return last_launch_status();
+}
+
 #define STAG_INSTANTIATE_MRHS_N(P, N)                                                                               \
   template int mdslash<P, N>(const stag_lattice_s*, SpinorM<P>, SpinorM<P>, int, const int*, cudaStream_t);         \
   template int mdslash_epi<P, N, 0>(const stag_lattice_s*, SpinorM<Acc<P>::value>, SpinorM<P>, int, SpinorM<P>,     \
                                     double, SpinorM<Acc<P>::value>, double, double, RedScratch, RedTarget,          \
                                     const int*, cudaStream_t);                                                      \
   template int tune_mrhs<P, N>(stag_lattice_s*, cudaStream_t);
+
+// the per-warp inner-product form (RED = 3) of the batched CG's operator
+#define STAG_INSTANTIATE_MRHS_RED3(P, N)                                                                            \
+  template int mdslash_epi<P, N, 3>(const stag_lattice_s*, SpinorM<Acc<P>::value>, SpinorM<P>, int, SpinorM<P>,     \
+                                    double, SpinorM<Acc<P>::value>, double, double, RedScratch, RedTarget,          \
+                                    const int*, cudaStream_t);                                                      \
+  template int launch_mcg_alpha_pw<P, N>(const stag_lattice_s*, const float2*, McgState*, cudaStream_t);
 
 }  // namespace stag
