@@ -214,25 +214,101 @@ def make_inputs():
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
-def cpu_baseline(fat, lng, b, iters_full, sample_iters=3):
+# The oracle as it stands, one process per source (spawned, so no GPU state
+# is inherited), the four sources solved side by side on four host cores;
+# the links reach the processes through shared memory, not by copy.
+_SHARED = {}
+
+
+def _oracle_worker_init(names, shape, dtype):
+    from multiprocessing import shared_memory
+
+    import numpy as np
+
+    for key, name in names.items():
+        shm = shared_memory.SharedMemory(name=name)
+        _SHARED[key] = (shm, np.ndarray(shape, dtype=dtype, buffer=shm.buf))
+
+
+def _oracle_worker_sample(args):
+    import oracle
+
+    b, sample_iters = args
+    t = time.perf_counter()
+    oracle.cg(_SHARED["fat"][1], _SHARED["lng"][1], b, MASS, DIMS, tol=TOL, max_iter=sample_iters)
+    return time.perf_counter() - t
+
+
+class OraclePool:
+    """Spawned worker processes holding the links (shared memory)."""
+
+    def __init__(self, fat, lng, workers):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+
+        import numpy as np
+
+        self.shms = []
+        names = {}
+        for key, a in (("fat", fat), ("lng", lng)):
+            shm = shared_memory.SharedMemory(create=True, size=a.nbytes)
+            np.ndarray(a.shape, dtype=a.dtype, buffer=shm.buf)[...] = a
+            self.shms.append(shm)
+            names[key] = shm.name
+        # one BLAS thread per worker: the workers are the parallelism
+        env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in env:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_worker_init,
+                                                     initargs=(names, fat.shape, fat.dtype))
+        finally:
+            for k, v in env.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.workers = workers
+
+    def sample(self, srcs, sample_iters):
+        """Wall time of `sample_iters` oracle CG iterations on every source at once."""
+        t = time.perf_counter()
+        per = self.pool.map(_oracle_worker_sample, [(b, sample_iters) for b in srcs])
+        return time.perf_counter() - t, per
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        for shm in self.shms:
+            shm.close()
+            shm.unlink()
+
+
+def cpu_baseline(fat, lng, srcs, iters_full, sample_iters=3, pool=None):
     """The FP64 numpy oracle, timed on a bounded sample and scaled to a solve.
 
     Runs `sample_iters` oracle CG iterations (each one operator application
-    plus vector updates) and one true-residual application, and scales the
-    time per application to the `iters_full` iterations of a full solve."""
-    import oracle
-
-    t = time.perf_counter()
-    oracle.cg(fat, lng, b, MASS, DIMS, tol=TOL, max_iter=sample_iters)
-    el = time.perf_counter() - t
-    per = el / (sample_iters + 1)
+    plus vector updates, and one true-residual application) on each source,
+    the sources in parallel processes, and scales the wall time per source to
+    the `iters_full` iterations of a full solve."""
+    own = pool is None
+    if own:
+        pool = OraclePool(fat, lng, min(len(srcs), os.cpu_count() or 1))
+    try:
+        pool.sample(srcs[:1], 1)  # workers started and the links attached before timing
+        wall, per = pool.sample(srcs, sample_iters)
+    finally:
+        if own:
+            pool.close()
+    per_source = wall / len(srcs)
     return {
-        "value": per * (iters_full + 1),
+        "value": per_source / (sample_iters + 1) * (iters_full + 1),
         "unit": "s",
-        "cores": 1,
+        "cores": pool.workers,
         "kind": "oracle",
-        "sample": f"{sample_iters} FP64 CG iterations of the numpy oracle on 32^4 source 0 "
-        f"({el:.1f} s), scaled to the {iters_full} iterations of a full FP64 solve",
+        "sample": f"{sample_iters} FP64 CG iterations of the numpy oracle on each of the {len(srcs)} 32^4 sources, "
+        f"one process per source on {pool.workers} host cores ({wall:.1f} s wall), per-source time scaled to "
+        f"the {iters_full} iterations of a full FP64 solve",
     }
 
 
@@ -302,6 +378,9 @@ def run_gpu(args, rank, world, local_rank):
     launches = stag.stag_launch_count() - launches0
     shapes = {k: stag.stag_tuned_shape(h, MODE_PREC[CHOSEN], i) for i, k in enumerate(("plain", "epilogue"))}
     mrhs_shape = stag.stag_tuned_mrhs(h, MODE_PREC[CHOSEN], NSRC) if BATCHED else None
+    mrhs_shape_epi = stag.stag_tuned_mrhs(h, MODE_PREC[CHOSEN], NSRC, epilogue=True) if BATCHED else None
+    mrhs_var = stag.stag_tuned_mrhs_variant(h, MODE_PREC[CHOSEN], NSRC) if BATCHED else None
+    mrhs_var_epi = stag.stag_tuned_mrhs_variant(h, MODE_PREC[CHOSEN], NSRC, epilogue=True) if BATCHED else None
     df_shape = stag.stag_tuned_shape(h, "df64", 0)
     n_d, ms_d = stag.stag_profile_read(fam_plain)
     n_e, ms_e = stag.stag_profile_read(fam_epi)
@@ -355,6 +434,8 @@ def run_gpu(args, rank, world, local_rank):
     if BATCHED:
         # one launch: the links once and NSRC input and output vectors
         bytes_launch = ((8 * 9 + 8 * nl) * ELEM_BYTES[prec] + 2 * NSRC * VEC_BYTES[prec]) * Vh
+        # template arguments of the launched kernel: format, Naik entries, N,
+        # threads per site, register cap
         kernel_id = f"k_dslash_mv<{pbits},{nl},{NSRC},{mrhs_shape[0]},{mrhs_shape[1]}>"
         sites_launch = NSRC * Vh
     else:
@@ -371,7 +452,7 @@ def run_gpu(args, rank, world, local_rank):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(fat, lng, srcs[0], iters_plain[0])
+            cpu = cpu_baseline(fat, lng, srcs, iters_plain[0])
         clocks = clk.summary()
         result = {
             "metric": METRIC,
@@ -416,11 +497,17 @@ def run_gpu(args, rank, world, local_rank):
                 "avg_launch_us": per_launch_ms * 1e3,
                 "gflops": FLOP_PER_SITE * sites_launch / (per_launch_ms * 1e-3) / 1e9,
                 "epilogue_variant_avg_us": ms_e / max(n_e, 1) * 1e3,
-                "launch_shape": ({"multi_rhs": {"block": 128, "threads_per_site": mrhs_shape[0],
+                "launch_shape": ({"multi_rhs": {"variant": mrhs_var, "block": 128, "threads_per_site": mrhs_shape[0],
                                                 "rhs_per_thread": NSRC // mrhs_shape[0],
                                                 "min_blocks_per_sm": mrhs_shape[1],
-                                                "tuned_us_per_operator": mrhs_shape[2],
-                                                "chosen_by": "autotuner (stag_tuned_mrhs)"}}
+                                                "tuned_us_per_launch": mrhs_shape[2],
+                                                "chosen_by": "autotuner (stag_tuned_mrhs)"},
+                                  "multi_rhs_epilogue": {"variant": mrhs_var_epi, "block": 128,
+                                                         "threads_per_site": mrhs_shape_epi[0],
+                                                         "rhs_per_thread": NSRC // mrhs_shape_epi[0],
+                                                         "min_blocks_per_sm": mrhs_shape_epi[1],
+                                                         "tuned_us_per_launch": mrhs_shape_epi[2],
+                                                         "chosen_by": "autotuner (stag_tuned_mrhs_epi)"}}
                                  if BATCHED else
                                  {k: {"block": v[0], "min_blocks_per_sm": v[1], "tuned_us": v[2]}
                                   for k, v in shapes.items()}),
@@ -469,10 +556,14 @@ def run_reference(args, rank, world):
     fat, lng, srcs = make_inputs()
     iters_full = ORACLE_FULL_ITERS
     times = []
-    for k in range(args.warmup + args.steps):
-        c = cpu_baseline(fat, lng, srcs[0], iters_full, sample_iters=2)
-        if k >= args.warmup:
-            times.append(c["value"])
+    pool = OraclePool(fat, lng, min(len(srcs), os.cpu_count() or 1))
+    try:
+        for k in range(args.warmup + args.steps):
+            c = cpu_baseline(fat, lng, srcs, iters_full, sample_iters=2, pool=pool)
+            if k >= args.warmup:
+                times.append(c["value"])
+    finally:
+        pool.close()
     v = statistics.mean(times)
     return {
         "impl": "reference",
@@ -676,15 +767,25 @@ def run_config(args):
         stag.stag_profile_reset()
         stag.stag_profile_enable(True)
         lg()
-        fam = {f: stag.stag_profile_read(f) for f in ("net", "net_bwd")}
+        fam = {f: stag.stag_profile_read(f) for f in ("net", "net_tc", "net_bwd")}
         stag.stag_profile_enable(False)
+        # the 16 -> 16 tensor-core layer against the HBM roofline: per site
+        # 8 fat hops of 72 B, the input record (384 B) and pre + output (768 B)
+        n_tc, ms_tc = fam["net_tc"]
+        tc_us = ms_tc / max(n_tc, 1) * 1e3
+        tc_bytes = 1728 * 2 * h.Vh
+        tc_roof = {"kernel": "k_net_layer_tc", "avg_launch_us": tc_us, "bytes_per_launch": tc_bytes,
+                   "achieved_gbs": tc_bytes / (tc_us * 1e-6) / 1e9 if tc_us > 0 else None}
+        if tc_roof["achieved_gbs"]:
+            peak, peak_kind = measured_peaks()
+            tc_roof.update(peak_gbs=peak, peak_kind=peak_kind, frac=tc_roof["achieved_gbs"] / peak)
         flops_fw = 0
         ch = (1, 16, 16, 16, 1)
         for l in range(4):
             # per site: 8 transports (66 flop) per input channel + 9 x Cin x Cout real-by-complex-3 mixes (12 flop)
             flops_fw += 2 * h.Vh * (8 * ch[l] * 66 + 9 * ch[l] * ch[l + 1] * 12)
         print(json.dumps({"config": f"network 1-16-16-16-1 on {args.net_dims}^4", "forward_s": t_f, "loss_grad_s": t_b,
-                          "forward_gflops": flops_fw / t_f / 1e9,
+                          "forward_gflops": flops_fw / t_f / 1e9, "tc_layer": tc_roof,
                           "families_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in fam.items()}}), flush=True)
         net.free()
         h.free()

@@ -165,19 +165,27 @@ int stag_free_lattice(stag_lattice_t lat);
  * NULL. */
 int stag_tuned_shape(stag_lattice_t lat, int prec, int kernel, int* block, int* min_blocks, double* us);
 
-/* The launch variant of the N-right-hand-side Dslash kernels (the operator
+/* The launch variant of the N-right-hand-side Dslash kernel (the operator
  * of stag_batch_solve and of stag_dslash with nrhs > 1) for groups of nrhs
  * = 2, 4 or 8 right-hand sides of format prec on this lattice: the threads
  * that share one site's right-hand sides (1, 2 or 4), the resident blocks
  * per SM promised to the compiler (1: no register cap; 4: at most 128
- * registers; 6: at most 80), and the timed cost of one operator application in us (0 when
+ * registers; 6: at most 80), and the timed cost of one launch in us (0 when
  * the variant was not timed: before the first such group, or with
- * autotune off).  The variant is chosen, the first time a group of that
- * size runs on a lattice of these extents, by timing every compiled variant
- * (the autotuner; the paper tunes nothing at run time, its QPhiX and QUDA
- * builds fix their blocking at compile time or tune it inside QUDA, Sec. 3).
- * EINVAL for another nrhs or a missing copy.  Any output may be NULL. */
+ * autotune off).  stag_tuned_mrhs reports the plain kernel (t = D_oe p),
+ * stag_tuned_mrhs_epi the epilogue form the batched CG runs (Ap = m^2 p -
+ * D_eo t with its <p, Ap> partials); each is chosen, the first time a group
+ * of that size runs on a lattice of these extents, by timing every compiled
+ * variant (the autotuner; the paper tunes nothing at run time, its QPhiX
+ * and QUDA builds fix their blocking at compile time or tune it inside
+ * QUDA, Sec. 3).  EINVAL for another nrhs or a missing copy.  Any output
+ * may be NULL. */
 int stag_tuned_mrhs(stag_lattice_t lat, int prec, int nrhs, int* threads_per_site, int* min_blocks, double* us);
+int stag_tuned_mrhs_epi(stag_lattice_t lat, int prec, int nrhs, int* threads_per_site, int* min_blocks, double* us);
+/* The same choice as a variant index (epilogue != 0: the epilogue form):
+ * 0..5 = (threads per site, min blocks) (1,1) (1,6) (2,4) (2,6) (4,4)
+ * (4,6).  Returns the index (>= 0) or STAG_EINVAL. */
+int stag_tuned_mrhs_variant(stag_lattice_t lat, int prec, int nrhs, int epilogue);
 
 /* The autotuner's cache (host only, no GPU call).  Tuned launches are kept
  * for the life of the process under a key naming the kernel family, the
@@ -542,7 +550,9 @@ const char* stag_strerror(int status);
  * "dslash64_epi" (FP64), "dslash_mrhs", "dslash_mrhs_epi", "dslash_mrhs64",
  * "dslash_mrhs64_epi" (multi-right-hand-side forms), "dslash_df",
  * "dslash_df_epi" (double-float), "blas", "reduce",
- * "convert", "links", "net", "net_bwd", "gauge_force", "fermion_force".  stag_launch_count
+ * "convert", "links", "net" (network forward layers), "net_tc" (the
+ * 16 -> 16 tensor-core layers of the forward), "net_bwd", "gauge_force",
+ * "fermion_force".  stag_launch_count
  * counts all library kernel launches since the last reset, whether or not
  * profiling is on. */
 int stag_profile_enable(int on);

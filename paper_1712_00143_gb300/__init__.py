@@ -78,6 +78,8 @@ EXPORTS = (
     "stag_profile_read",
     "stag_launch_count",
     "stag_tuned_mrhs",
+    "stag_tuned_mrhs_epi",
+    "stag_tuned_mrhs_variant",
     "stag_tune_key",
     "stag_tune_cache_get",
     "stag_tune_cache_put",
@@ -212,6 +214,8 @@ def load_library(path=LIB_PATH):
         "stag_profile_read": (ci, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(cd)]),
         "stag_launch_count": (ctypes.c_longlong, []),
         "stag_tuned_mrhs": (ci, [vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(cd)]),
+        "stag_tuned_mrhs_epi": (ci, [vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(cd)]),
+        "stag_tuned_mrhs_variant": (ci, [vp, ci, ci, ci]),
         "stag_tune_key": (ci, [ctypes.c_char_p, ci, ctypes.c_char_p, ci, ci, ci, ctypes.POINTER(ci)]),
         "stag_tune_cache_get": (ci, [ctypes.c_char_p, ctypes.POINTER(ci), ctypes.POINTER(cd)]),
         "stag_tune_cache_put": (ci, [ctypes.c_char_p, ci, cd]),
@@ -605,13 +609,28 @@ def stag_launch_count():
     return int(_lib.stag_launch_count())
 
 
-def stag_tuned_mrhs(h, prec, nrhs):
-    """(threads per site, min blocks per SM, us per operator application) of
-    the N-right-hand-side kernels' tuned launch variant (us 0: not timed)."""
+def stag_tuned_mrhs(h, prec, nrhs, epilogue=False):
+    """(threads per site, min blocks per SM, us per launch) of the tuned
+    launch variant of the N-right-hand-side plain kernel, or with
+    epilogue=True of its epilogue form (us 0: not timed)."""
     t, m, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-    _check(_lib.stag_tuned_mrhs(h.ptr, _prec(prec), int(nrhs), ctypes.byref(t), ctypes.byref(m), ctypes.byref(us)),
-           "stag_tuned_mrhs")
+    fn = _lib.stag_tuned_mrhs_epi if epilogue else _lib.stag_tuned_mrhs
+    _check(fn(h.ptr, _prec(prec), int(nrhs), ctypes.byref(t), ctypes.byref(m), ctypes.byref(us)),
+           "stag_tuned_mrhs_epi" if epilogue else "stag_tuned_mrhs")
     return t.value, m.value, us.value
+
+
+def stag_tuned_mrhs_epi(h, prec, nrhs):
+    return stag_tuned_mrhs(h, prec, nrhs, epilogue=True)
+
+
+def stag_tuned_mrhs_variant(h, prec, nrhs, epilogue=False):
+    """Index (0..5) of the tuned variant of the N-right-hand-side plain kernel
+    or of its epilogue form."""
+    v = int(_lib.stag_tuned_mrhs_variant(h.ptr, _prec(prec), int(nrhs), 1 if epilogue else 0))
+    if v < 0:
+        raise StagError(v, "stag_tuned_mrhs_variant")
+    return v
 
 
 def stag_tune_key(kernel, prec, nl, nrhs, dims):

@@ -153,7 +153,7 @@ template <int P, int N> struct Group : GroupBase {
   // the anchor (ya64, its residual radf; see McgState), y - ya, the odd
   // intermediate and the residual
   bool use_df = false;
-  float2* pw = nullptr;  // per-warp partials of <p, Ap> (FP32-arithmetic formats)
+  float* pt = nullptr;  // per-site values of <p, Ap> (FP32-arithmetic formats)
   SpinorM<64> ya64;
   DfField radf, ydf, tdf, rdf;
   RedScratch rs;
@@ -184,7 +184,7 @@ template <int P, int N> struct Group : GroupBase {
     }
     t64 = ws_spinorm<64>(lat, pre + "t64", N, &s);
     r64 = ws_spinorm<64>(lat, pre + "r64", N, &s);
-    pw = (float2*)lat->ws.get(pre + "pw", sizeof(float2) * N * ((size_t)Vh / 32 + 4), &s);
+    pt = (float*)lat->ws.get(pre + "pt", sizeof(float) * N * (size_t)Vh, &s);
     dst = (McgState*)lat->ws.get(pre + "state", sizeof(McgState), &s);
     dscal = (double*)lat->ws.get(pre + "scal", sizeof(double) * 2 * MAX_RHS, &s);
     if (s) return s;
@@ -316,17 +316,18 @@ template <int P, int N> struct Group : GroupBase {
   }
 
   // Ap = shift p - D_eo t and <p_r, Ap_r> -> alpha_r.  FP32-arithmetic
-  // formats: the operator kernel leaves per-warp double-float partials of
-  // <p, Ap> (no block barrier, no extra pass) and one small block sums them;
-  // FP64: the operator without a reduction, then <p, Ap> in a level-1 pass
-  // (a block-tree reduction fused into the operator grid, 4096 blocks at
-  // 32^4, held every block until its slowest warp was done: measured slower)
+  // formats: the operator kernel also stores each site's <p_r, Ap_r> (4
+  // bytes per site and system) and a small grid sum reads those instead of
+  // p and Ap; FP64: the operator without a reduction, then <p, Ap> in a
+  // level-1 pass.  (A block-tree reduction fused into the operator grid,
+  // 4096 blocks at 32^4, held every block until its slowest warp was done:
+  // measured slower than either.)
   int operator_epilogue(SpinorM<PV> none, const int* flags) {
     const int Vh = lat->g.Vh;
     if constexpr (P != 64) {
-      TRYB((mdslash_epi<P, N, 3>(lat, Ap, t, 0, p, shift, none, 0.0, -1.0, RedScratch{(double*)pw, nullptr, 0},
+      TRYB((mdslash_epi<P, N, 3>(lat, Ap, t, 0, p, shift, none, 0.0, -1.0, RedScratch{(double*)pt, nullptr, 0},
                                  RedTarget{RED_STORE, nullptr, nullptr}, flags, st)));
-      return launch_mcg_alpha_pw<P, N>(lat, pw, dst, st);
+      return launch_mcg_alpha_pt<P, N>(lat, pt, dst, rs, st);
     } else {
       TRYB((mdslash_epi<P, N, 0>(lat, Ap, t, 0, p, shift, none, 0.0, -1.0, rs, RedTarget{RED_STORE, nullptr, nullptr},
                                  flags, st)));

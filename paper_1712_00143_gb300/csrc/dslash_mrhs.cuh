@@ -54,9 +54,9 @@ int mdslash_epi(const stag_lattice_s* lat, SpinorM<Acc<P>::value> out, SpinorM<P
                 double ax, SpinorM<Acc<P>::value> y, double ay, double ad, RedScratch rs, RedTarget tgt,
                 const int* flags, cudaStream_t st);
 template <int P, int N> int tune_mrhs(stag_lattice_s* lat, cudaStream_t st);
-// <p_r, Ap_r> -> RED_MCG_ALPHA from the per-warp partials of mdslash_epi<P, N, 3>
+// <p_r, Ap_r> -> RED_MCG_ALPHA from the per-site values of mdslash_epi<P, N, 3>
 template <int P, int N>
-int launch_mcg_alpha_pw(const stag_lattice_s* lat, const float2* pw, McgState* g, cudaStream_t st);
+int launch_mcg_alpha_pt(const stag_lattice_s* lat, const float* pt, McgState* g, RedScratch rs, cudaStream_t st);
 
 template <int P> struct DslashArgsM {
   Geom g;

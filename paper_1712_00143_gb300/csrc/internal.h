@@ -48,11 +48,14 @@ struct stag_lattice_s {
   int dims[4];
   double c3 = -1.0 / 24.0;
   int autotune = 1;  // time launch variants on this lattice (stag_link_opts.autotune)
-  // launch variant of the N-right-hand-side kernels per (format, N = 2, 4, 8)
-  // (-1: not chosen yet) and its time per operator application (us)
+  // launch variants of the N-right-hand-side kernels per (format, N = 2, 4,
+  // 8): the plain operator half and the epilogue form the batched CG runs
+  // (-1: not chosen yet), each with its time per launch (us)
   struct MrhsTune {
     int variant = -1;
     float us = 0.f;
+    int variant_epi = -1;
+    float us_epi = 0.f;
   } mrhs[6][4];  // by the ABI precision (stag_prec), tuned per format
   stag::LinkCopy links[5];  // by stag_prec (STAG_DF64 = 4: FP64 split into hi + lo floats)
   stag::Workspace ws;

@@ -27,7 +27,11 @@ struct MVariant {
 };
 // {1,1} {1,6} {2,4} {2,6} {4,4} {4,6}: without a cap the compiler takes
 // 140-170 registers (three blocks per SM) whatever the split, so the split
-// variants are capped at 128 (4 blocks) or 80 (6 blocks) registers
+// variants are capped at 128 (4 blocks) or 80 (6 blocks) registers.  Two
+// more forms of {1,x} were measured at 32^4, N = 4, and removed: each
+// thread's link chunks staged one direction ahead in shared memory with
+// asynchronous copies (three blocks per SM; 128 us per launch against 117),
+// and a bulk L2 prefetch of the block's next-direction links (130 us).
 __host__ __device__ constexpr MVariant mvariant(int v) {
   return MVariant{v < 2 ? 1 : v < 4 ? 2 : 4, (v & 1) ? 6 : v == 0 ? 1 : 4};
 }
@@ -71,10 +75,15 @@ __global__ void __launch_bounds__(MB, MINB) k_dslash_mv(DslashArgsM<P> a, Spinor
 
 // out_r = ax x_r + ay y_r + ad (D in)_r; RED = 1: Re<x_r, out_r>, RED = 2:
 // ||out_r||^2, one sum per system, finalised by the last block (needs SP = 1:
-// the block's threads hold the sums of one system each).  RED = 3:
-// Re<x_r, out_r> as per-warp double-float partials in rb.partials (float2
-// [N][W], W warps of site coverage; no block barrier, no last block), summed
-// by k_mcg_alpha_pw: the batched CG's <p, Ap> without a pass of its own.
+// the block's threads hold the sums of one system each).  RED = 3: the
+// site's Re<x_r, out_r> stored per site, float [N][Vh] in rb.partials (its
+// six products summed in FP32: an error of a few units in the last place of
+// the sum of their magnitudes, the level of the FP32 operands themselves),
+// summed over sites by k_mcg_alpha_pt: the batched CG's <p, Ap> without
+// reading p and Ap back (4 bytes per site and system against 48).  No
+// barrier, no shuffle and nothing after the site's branch: every form that
+// kept a sum live past the stencil (per-warp sums, double-float per-thread
+// sums) made the compiler spill at the 80-register cap.
 template <int P, int NL, int N, int RED, int SP, int MINB>
 __global__ void __launch_bounds__(MB, MINB)
     k_dslash_m_epi_v(DslashArgsM<P> a, SpinorM<Acc<P>::value> out, SpinorM<P> x, double ax,
@@ -122,28 +131,24 @@ __global__ void __launch_bounds__(MB, MINB)
         }
       }
       SpinorLoadM<PA>::st(out, s, r, o);
-      if (RED) {
+      if constexpr (RED == 3) {
+        float d3 = 0.f;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          red[r].add_prod(RED == 2 ? o[i].x : xv[i].x, o[i].x);  // RED 1 and 3: <x, out>
-          red[r].add_prod(RED == 2 ? o[i].y : xv[i].y, o[i].y);
+          d3 = fmaf((float)xv[i].x, (float)o[i].x, d3);
+          d3 = fmaf((float)xv[i].y, (float)o[i].y, d3);
+        }
+        ((float*)rb.partials)[(size_t)(part * NT + r) * a.g.Vh + s] = d3;
+      } else if constexpr (RED != 0) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          red[r].add_prod(RED == 1 ? xv[i].x : o[i].x, o[i].x);
+          red[r].add_prod(RED == 1 ? xv[i].y : o[i].y, o[i].y);
         }
       }
     }
   }
-  if constexpr (RED == 3) {
-    DF v[NT];
-#pragma unroll
-    for (int r = 0; r < NT; ++r) v[r] = red[r].v;
-    warp_sum_df<NT>(v);
-    if ((threadIdx.x & 31) == 0) {
-      const int W = gridDim.x * (SPB / 32);
-      const int w = blockIdx.x * (SPB / 32) + ((threadIdx.x - part * SPB) >> 5);
-      float2* pw = (float2*)rb.partials;
-#pragma unroll
-      for (int r = 0; r < NT; ++r) pw[(size_t)(part * NT + r) * W + w] = make_float2(v[r].hi, v[r].lo);
-    }
-  } else if constexpr (RED != 0) {
+  if constexpr (RED != 0 && RED != 3) {
     grid_reduce_acc<N>(red, rb, tgt);
   }
 }
@@ -163,9 +168,14 @@ template <int P> DslashArgsM<P> make_args_m(const stag_lattice_s* lat, SpinorM<P
 
 __host__ __device__ constexpr int mrhs_nindex(int n) { return n == 2 ? 0 : n == 4 ? 1 : n == 8 ? 2 : 3; }
 
-// The variant a group of N right-hand sides of format P runs with on this lattice.
+// The variants a group of N right-hand sides of format P runs with on this
+// lattice: the plain operator half, and the epilogue form.
 template <int P, int N> int mrhs_variant(const stag_lattice_s* lat) {
   const int v = lat->mrhs[abi_prec<P>()][mrhs_nindex(N)].variant;
+  return v >= 0 ? v : mrhs_default_variant(P, N);
+}
+template <int P, int N> int mrhs_variant_epi(const stag_lattice_s* lat) {
+  const int v = lat->mrhs[abi_prec<P>()][mrhs_nindex(N)].variant_epi;
   return v >= 0 ? v : mrhs_default_variant(P, N);
 }
 
@@ -263,44 +273,55 @@ template <int P, int N, int RED>
 int mdslash_epi(const stag_lattice_s* lat, SpinorM<Acc<P>::value> out, SpinorM<P> in, int out_parity, SpinorM<P> x,
                 double ax, SpinorM<Acc<P>::value> y, double ay, double ad, RedScratch rs, RedTarget tgt,
                 const int* flags, cudaStream_t st) {
-  return mdslash_epi_v<P, N, RED>(lat, mrhs_variant<P, N>(lat), out, in, out_parity, x, ax, y, ay, ad, rs, tgt, flags,
-                                  st);
+  return mdslash_epi_v<P, N, RED>(lat, mrhs_variant_epi<P, N>(lat), out, in, out_parity, x, ax, y, ay, ad, rs, tgt,
+                                  flags, st);
 }
 
 // The autotuner of the N-right-hand-side kernels: on the first group of N
 // right-hand sides of format P on a lattice, time every built variant of the
-// plain and the epilogue kernel (one warm-up and three timed pairs, the
-// operator's two halves t = D_oe p, Ap = m^2 p - D_eo t, on scratch vectors)
-// and keep the fastest pair.  The choice is looked up first, and recorded,
-// in the process-wide cache under the key (kernel, format, Naik storage, N,
-// extents).  Must not run while a stream is being captured.
+// plain operator half (t = D_oe p) and, separately, of the epilogue form the
+// batched CG runs (Ap = m^2 p - D_eo t with the per-site <p, Ap> values for
+// the FP32-arithmetic formats), one warm-up and three timed launches each on
+// scratch vectors, and keep the fastest of each (a variant's register cap
+// can suit one form and not the other).  The choices are looked up first,
+// and recorded, in the process-wide cache under the keys ("dslash_mrhs" or
+// "dslash_mrhs_epi", format, Naik storage, N, extents).  Must not run while
+// a stream is being captured.
 template <int P, int N> int tune_mrhs(stag_lattice_s* lat, cudaStream_t st) {
   auto& slot = lat->mrhs[abi_prec<P>()][mrhs_nindex(N)];
-  if (slot.variant >= 0) return STAG_OK;
+  if (slot.variant >= 0 && slot.variant_epi >= 0) return STAG_OK;
   const LinkCopy& L = lat->links[prec_index<P>()];
   if (!L.present) return STAG_EINVAL;
   const int def = mrhs_default_variant(P, N);
   if (!lat->autotune || P == 64) {
-    slot.variant = def;
+    slot.variant = slot.variant_epi = def;
     return STAG_OK;
   }
   const std::string key = tune_key("dslash_mrhs", abi_prec<P>(), L.nl, N, lat->dims);
-  int cached = -1;
-  double cached_us = 0.0;
-  if (tune_cache_get(key, &cached, &cached_us) && cached >= 0 && cached < kNumMVariants &&
-      mrhs_variant_built(P, L.nl, N, cached)) {
-    slot.variant = cached;
-    slot.us = (float)cached_us;
-    return STAG_OK;
-  }
+  const std::string key_epi = tune_key("dslash_mrhs_epi", abi_prec<P>(), L.nl, N, lat->dims);
+  auto cached = [&](const std::string& k, int* v, float* us) {
+    int c = -1;
+    double cu = 0.0;
+    if (tune_cache_get(k, &c, &cu) && c >= 0 && c < kNumMVariants && mrhs_variant_built(P, L.nl, N, c)) {
+      *v = c;
+      *us = (float)cu;
+    }
+  };
+  if (slot.variant < 0) cached(key, &slot.variant, &slot.us);
+  if (slot.variant_epi < 0) cached(key_epi, &slot.variant_epi, &slot.us_epi);
+  if (slot.variant >= 0 && slot.variant_epi >= 0) return STAG_OK;
+
   constexpr int PA = Acc<P>::value;
+  constexpr int RED = P == 64 ? 0 : 3;
   const int Vh = lat->g.Vh;
   int s = 0;
   SpinorM<P> in{lat->ws.get("tunem.in", spinorm_bytes<P>(Vh, N), &s), Vh, N};
   SpinorM<P> t{lat->ws.get("tunem.t", spinorm_bytes<P>(Vh, N), &s), Vh, N};
   SpinorM<PA> o{lat->ws.get("tunem.o", spinorm_bytes<PA>(Vh, N), &s), Vh, N};
+  double* pw = (double*)lat->ws.get("tunem.pw", sizeof(float) * N * (size_t)Vh, &s);
   if (s) return s;
   if ((s = cuda_status(cudaMemsetAsync(in.v, 0, spinorm_bytes<P>(Vh, N), st)))) return s;
+  if ((s = cuda_status(cudaMemsetAsync(t.v, 0, spinorm_bytes<P>(Vh, N), st)))) return s;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     cudaGetLastError();
@@ -308,26 +329,43 @@ template <int P, int N> int tune_mrhs(stag_lattice_s* lat, cudaStream_t st) {
     return STAG_ECUDA;
   }
   const int reps = 3;
-  float best = 1e30f;
-  int pick = def;
   SpinorM<PA> none{nullptr, Vh, N};
-  RedScratch rs{nullptr, nullptr, 1 << 30};
-  for (int v = 0; v < kNumMVariants && !s; ++v) {
-    if (!mrhs_variant_built(P, L.nl, N, v)) continue;
-    for (int it = -1; it < reps && !s; ++it) {
-      if (it == 0) s = cuda_status(cudaEventRecord(e0, st));
-      if (!s) s = mdslash_v<P, N>(lat, v, t, in, 1, nullptr, st);
-      if (!s)
-        s = mdslash_epi_v<P, N, 0>(lat, v, o, t, 0, in, 0.01, none, 0.0, -1.0, rs,
-                                   RedTarget{RED_STORE, nullptr, nullptr}, nullptr, st);
+  RedScratch rs{pw, nullptr, 1 << 30};
+  // form 0: plain, form 1: epilogue
+  for (int form = 0; form < 2 && !s; ++form) {
+    if ((form == 0 ? slot.variant : slot.variant_epi) >= 0) continue;
+    float best = 1e30f;
+    int pick = def;
+    for (int v = 0; v < kNumMVariants && !s; ++v) {
+      if (!mrhs_variant_built(P, L.nl, N, v)) continue;
+      for (int it = -1; it < reps && !s; ++it) {
+        if (it == 0) s = cuda_status(cudaEventRecord(e0, st));
+        if (s) break;
+        if (form == 0)
+          s = mdslash_v<P, N>(lat, v, t, in, 1, nullptr, st);
+        else
+          s = mdslash_epi_v<P, N, RED>(lat, v, o, t, 0, in, 0.01, none, 0.0, -1.0, rs,
+                                       RedTarget{RED_STORE, nullptr, nullptr}, nullptr, st);
+      }
+      float ms = 0.f;
+      if (!s) s = cuda_status(cudaEventRecord(e1, st));
+      if (!s) s = cuda_status(cudaEventSynchronize(e1));
+      if (!s) s = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+      if (!s && ms < best) {
+        best = ms;
+        pick = v;
+      }
     }
-    float ms = 0.f;
-    if (!s) s = cuda_status(cudaEventRecord(e1, st));
-    if (!s) s = cuda_status(cudaEventSynchronize(e1));
-    if (!s) s = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
-    if (!s && ms < best) {
-      best = ms;
-      pick = v;
+    if (s) break;
+    const float us = best * 1e3f / reps;
+    if (form == 0) {
+      slot.variant = pick;
+      slot.us = us;
+      tune_cache_put(key, pick, us);
+    } else {
+      slot.variant_epi = pick;
+      slot.us_epi = us;
+      tune_cache_put(key_epi, pick, us);
     }
   }
   cudaEventDestroy(e0);
@@ -335,48 +373,46 @@ template <int P, int N> int tune_mrhs(stag_lattice_s* lat, cudaStream_t st) {
   lat->ws.drop("tunem.in");
   lat->ws.drop("tunem.t");
   lat->ws.drop("tunem.o");
-  if (s) return s;
-  slot.variant = pick;
-  slot.us = best * 1e3f / reps;  // one operator (plain + epilogue launch)
-  tune_cache_put(key, pick, slot.us);
-  return STAG_OK;
+  lat->ws.drop("tunem.pw");
+  return s;
 }
 
-// Per-warp partials of a RED = 3 launch for N right-hand sides of format P:
-// W = the warps of one part (right-hand-side share) over the grid; at most
-// Vh / 32 + 3.
-template <int P, int N> int mrhs_partial_warps(const stag_lattice_s* lat) {
-  const int spb = MB / mvariant(mrhs_variant<P, N>(lat)).sp;
-  return (lat->g.Vh + spb - 1) / spb * (spb / 32);
-}
-
-// <p_r, Ap_r> of every system from the per-warp partials of a RED = 3
-// operator launch (float2 [N][W]): one block, double-float sums in a fixed
-// order, then RED_MCG_ALPHA.  Nothing once the group's stop word is set.
-template <int N> __global__ void __launch_bounds__(512) k_mcg_alpha_pw(const float2* pw, int W, McgState* g) {
+// <p_r, Ap_r> of every system from the per-site values of a RED = 3
+// operator launch (float [N][Vh]): per-thread double-float sums over a
+// grid-stride range of sites, then the library's deterministic grid sum and
+// RED_MCG_ALPHA.  Nothing once the group's stop word is set.
+template <int N>
+__global__ void __launch_bounds__(256) k_mcg_alpha_pt(const float* __restrict__ pt, int Vh, McgState* g, RedBuf rb) {
   if (stopped(&g->flags)) return;
+  constexpr int U = 4;  // sites per thread and pass, loaded before they are added
   DF v[N];
 #pragma unroll
   for (int r = 0; r < N; ++r) v[r] = DF{0.f, 0.f};
-  for (int w = threadIdx.x; w < W; w += blockDim.x)
+  const int stride = gridDim.x * blockDim.x;
+  for (int s0 = blockIdx.x * blockDim.x + threadIdx.x; s0 < Vh; s0 += U * stride) {
+    float q[U][N];
 #pragma unroll
-    for (int r = 0; r < N; ++r) {
-      const float2 q = __ldcg(pw + (size_t)r * W + w);
-      df_add_df(v[r], DF{q.x, q.y});
-    }
-  block_sum_df<N>(v);
-  if (threadIdx.x == 0) {
-    double t[N];
+    for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int r = 0; r < N; ++r) t[r] = df_value(v[r]);
-    finalize(RedTarget{RED_MCG_ALPHA, g, nullptr}, t, N);
+      for (int r = 0; r < N; ++r) {
+        const int s = s0 + u * stride;
+        q[u][r] = s < Vh ? __ldcg(pt + (size_t)r * Vh + s) : 0.f;
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < N; ++r) df_add_df(v[r], DF{q[u][r], 0.f});
   }
+  grid_reduce_df<N>(v, rb, RedTarget{RED_MCG_ALPHA, g, nullptr});
 }
 
 template <int P, int N>
-int launch_mcg_alpha_pw(const stag_lattice_s* lat, const float2* pw, McgState* g, cudaStream_t st) {
+int launch_mcg_alpha_pt(const stag_lattice_s* lat, const float* pt, McgState* g, RedScratch rs, cudaStream_t st) {
+  const int Vh = lat->g.Vh;
+  int G = (Vh + 4 * 256 - 1) / (4 * 256);  // four sites per thread
+  G = G < 1 ? 1 : G > rs.max_grid ? rs.max_grid : G;
   ProfScope ps("reduce", st);
-  k_mcg_alpha_pw<N><<<1, 512, 0, st>>>(pw, mrhs_partial_warps<P, N>(lat), g);
+  k_mcg_alpha_pt<N><<<G, 256, 0, st>>>(pt, Vh, g, RedBuf{rs.partials, rs.counter});
   return last_launch_status();
 }
 
@@ -392,6 +428,6 @@ int launch_mcg_alpha_pw(const stag_lattice_s* lat, const float2* pw, McgState* g
   template int mdslash_epi<P, N, 3>(const stag_lattice_s*, SpinorM<Acc<P>::value>, SpinorM<P>, int, SpinorM<P>,     \
                                     double, SpinorM<Acc<P>::value>, double, double, RedScratch, RedTarget,          \
                                     const int*, cudaStream_t);                                                      \
-  template int launch_mcg_alpha_pw<P, N>(const stag_lattice_s*, const float2*, McgState*, cudaStream_t);
+  template int launch_mcg_alpha_pt<P, N>(const stag_lattice_s*, const float*, McgState*, RedScratch, cudaStream_t);
 
 }  // namespace stag

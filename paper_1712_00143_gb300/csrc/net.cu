@@ -241,11 +241,11 @@ static void launch_layer(const NetRun& R, int l, const float2* in, float2* pre, 
     // one CTA per 64-site tile
     static bool attr[2] = {false, false};
     if (!attr[GATE]) {
-      cudaFuncSetAttribute(k_net_layer_tc<GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+      cudaFuncSetAttribute(k_net_layer_tc<GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::LAYER_SMEM);
       attr[GATE] = true;
     }
     const int tiles = 2 * ((R.Vh + tc::TILE - 1) / tc::TILE);
-    k_net_layer_tc<GATE><<<tiles, 128, tc::SMEM_BYTES, st>>>(R.ng, in, pre, out, W, b, transpose);
+    k_net_layer_tc<GATE><<<tiles, 128, tc::LAYER_SMEM, st>>>(R.ng, in, pre, out, W, b, transpose);
   } else if constexpr (COUT == 1 && CIN == 16 && !GATE) {
     if (!transpose) {
       // one output channel: site-local mix into the nine directions, then
@@ -293,7 +293,7 @@ static int layer_fwd(const NetRun& R, int l, cudaStream_t st) {
   const __nv_bfloat16* W = N->wb + N->woff[l];
   const float* b = gate ? N->w + N->boff[l] : nullptr;
   float2 *in = R.h[l], *out = R.h[l + 1], *pre = gate ? R.pre[l + 1] : R.h[l + 1];
-  ProfScope ps("net", st);
+  ProfScope ps(ci == 16 && co == 16 ? "net_tc" : "net", st);
   if (ci == 1 && co == 16 && gate) launch_layer<1, 16, true>(R, l, in, pre, out, W, b, 0, st);
   else if (ci == 16 && co == 16 && gate) launch_layer<16, 16, true>(R, l, in, pre, out, W, b, 0, st);
   else if (ci == 16 && co == 1 && !gate) launch_layer<16, 1, false>(R, l, in, pre, out, W, b, 0, st);

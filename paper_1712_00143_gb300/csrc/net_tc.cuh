@@ -156,21 +156,68 @@ __device__ int g_tc_error;  // set (never cleared by kernels) when a bounded wai
 
 constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds at GB300 clocks
 
+// ---- layout of the layer kernel's shared memory (bytes from the 1024-aligned base)
+constexpr int REC = 16 * 3 * 8;                      // one site's 16 input channels: 384 B
+constexpr int REC_CHUNKS = REC / 16;                 // 24 chunks of 16 B
+constexpr int S_BYTES = TILE * REC;                  // one staged direction: 24576 B
+constexpr int L_A = 0;                               // A operand, hi and lo parts
+constexpr int L_S = L_A + 2 * A_BYTES;               // staged neighbour records, two directions
+constexpr int L_B = L_S + 2 * S_BYTES;               // B operand of the current direction
+constexpr int L_NB = L_B + B_BYTES;                  // neighbour table int [9][TILE]
+constexpr int L_BAR = L_NB + NET_NDIR * TILE * 4;    // mbarrier, tensor-memory slot, status
+constexpr int LAYER_SMEM = L_BAR + 64;               // 76608 B: three CTAs per SM
+
+static_assert(TILE * E_STRIDE * 4 <= 2 * S_BYTES, "epilogue staging must fit in the record buffers");
+static_assert(L_S % 16 == 0 && L_B % 16 == 0 && L_BAR % 8 == 0, "alignment");
+
+// Chunk q of staged record r: the low three bits of the chunk index are
+// XORed with the record's, so that eight consecutive records read at one
+// chunk index fall in eight different 16-byte bank groups.
+__device__ __forceinline__ uint32_t rec_off(int r, int q) {
+  return (uint32_t)(r * REC + (((q & ~7) | ((q ^ r) & 7)) << 4));
+}
+
+// 16-byte asynchronous copy global -> shared (src_bytes 0: zero fill).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ float4 ld_shared_v4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+  return v;
+}
+
 }  // namespace tc
 
 // 16 -> 16 layer on the tensor cores.  transpose != 0: the adjoint layer
 // (weights W'[d][c][c'] = sign(d) W[partner(d)][c'][c]).  GATE: hout =
 // pre * sigmoid(|pre|^2 - b_c) and pre stored; else hout = pre.
+//
+// Per direction d the CTA (64 sites of one parity, 128 threads) needs the
+// 384-byte input records of the 64 neighbour sites.  They are copied into
+// shared memory with 16-byte asynchronous copies one direction ahead (a
+// warp's copies cover 512 contiguous bytes when the neighbours are
+// consecutive sites), so that the gather of d + 1 is in flight while the
+// CUDA cores transport direction d and the tensor cores mix it; the link
+// matrix of d + 1 is prefetched into registers the same way.  The A and B
+// operands are single-buffered: the MMAs of d - 1 (a few hundred cycles)
+// are complete long before the transports of d are, and the smaller
+// footprint lets three CTAs share an SM.  Input activations must be 16-byte
+// aligned (every workspace buffer is).
 template <bool GATE>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, 3)
     k_net_layer_tc(NetGeom ng, const float2* __restrict__ hin, float2* __restrict__ pre, float2* __restrict__ hout,
                    const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias, int transpose) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  unsigned char* A = tc_smem;                                // [buffer 2][part 2][A_BYTES]
-  unsigned char* Bw = tc_smem + 4 * A_BYTES;                 // [9][B_BYTES]
-  uint64_t* bar = (uint64_t*)(Bw + NET_NDIR * B_BYTES);   // [2]
-  uint32_t* tmem_slot = (uint32_t*)(bar + 2);
+  int* nb = (int*)(tc_smem + L_NB);                        // [9][TILE] neighbour site, -1 past the end
+  uint64_t* bar = (uint64_t*)(tc_smem + L_BAR);
+  uint32_t* tmem_slot = (uint32_t*)(bar + 1);
   int* s_ok = (int*)(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -179,21 +226,18 @@ __global__ void __launch_bounds__(128, 4)
   const int p = blockIdx.x / tiles_per_parity;
   const int s0 = (blockIdx.x - p * tiles_per_parity) * TILE;
 
-  // weights -> B operand (N = output channel c, K = input channel c')
-  for (int i = tid; i < NET_NDIR * 256; i += blockDim.x) {
-    const int d = i >> 8, c = (i >> 4) & 15, cp = i & 15;
-    float w;
-    if (!transpose) {
-      w = __bfloat162float(W[i]);
-    } else {
-      const int dd = d == 0 ? 0 : ((d & 1) ? d + 1 : d - 1);
-      w = (d == 0 ? 1.f : -1.f) * __bfloat162float(W[(dd * 16 + cp) * 16 + c]);
-    }
-    *(__nv_bfloat16*)(Bw + d * B_BYTES + op_offset(c, cp)) = __float2bfloat16_rn(w);
+  // staging role: site s_local, channel half `half` (8 input channels)
+  const int s_local = tid & 63, half = tid >> 6;
+  const int s = s0 + s_local;
+  const bool valid = s < Vh;
+  {
+    const Coord crd = valid ? cb_coords(ng.g, s, p) : Coord{0, 0, 0, 0};
+    for (int d = half ? 5 : 0; d < (half ? NET_NDIR : 5); ++d)
+      nb[d * TILE + s_local] =
+          !valid ? -1 : d == 0 ? s : cb_neighbour(ng.g, s, crd, (d - 1) >> 1, (d & 1) ? 1 : -1);
   }
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    mbar_init(bar, 1);
     *s_ok = 1;
     fence_barrier_init();
   }
@@ -203,69 +247,85 @@ __global__ void __launch_bounds__(128, 4)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   constexpr uint32_t IDESC = idesc_bf16(128, 16);
+  const uint32_t base = smem_u32(tc_smem);
+  const uint32_t hi_base = base + L_A, lo_base = base + L_A + A_BYTES;
 
-  // staging role: site s_local, channel half `half` (8 input channels)
-  const int s_local = tid & 63, half = tid >> 6;
-  const int s = s0 + s_local;
-  const bool valid = s < Vh;
-  const uint32_t a_base = smem_u32(A);
-  const Coord crd = valid ? cb_coords(ng.g, s, p) : Coord{0, 0, 0, 0};  // once, not per direction
+  // the 64 records of direction d -> record buffer b: chunk i = k * 128 + tid
+  auto stage = [&](int d, int b) {
+    const uint32_t sb = base + L_S + (uint32_t)b * S_BYTES;
+    const char* src0 = (const char*)act_ptr(hin, 16, Vh, d ? 1 - p : p, 0);
+#pragma unroll
+    for (int k = 0; k < TILE * REC_CHUNKS / 128; ++k) {
+      const int i = k * 128 + tid;
+      const int r = i / REC_CHUNKS, q = i - r * REC_CHUNKS;
+      const int ns = nb[d * TILE + r];
+      const char* src = ns >= 0 ? src0 + (size_t)ns * REC + q * 16 : (const char*)hin;
+      cp_async16(sb + rec_off(r, q), src, ns >= 0 ? 16u : 0u);
+    }
+    cp_async_commit();
+  };
+
+  stage(0, 0);
+  float2 w[9], wn[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) w[e] = wn[e] = make_float2(0.f, 0.f);
 
 #pragma unroll 1
   for (int d = 0; d < NET_NDIR; ++d) {
     const int buf = d & 1;
-    if (d >= 2) {
-      // the MMAs of direction d - 2 read this buffer: wait for them
-      if (tid == 0 && *s_ok && !mbar_wait(&bar[buf], (uint32_t)(((d - 2) >> 1) & 1), WAIT_CYCLES)) *s_ok = 0;
-      __syncthreads();
+    if (d + 1 < NET_NDIR) {
+      // the record buffer of d + 1 was last read by the transports of d - 1,
+      // which every thread finished before the barrier ahead of that MMA
+      stage(d + 1, buf ^ 1);
+      if (valid) load_hop_matrix(ng, p, s, d + 1, wn);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
-    const uint32_t hi_base = a_base + (uint32_t)(buf * 2 + 0) * A_BYTES;
-    const uint32_t lo_base = a_base + (uint32_t)(buf * 2 + 1) * A_BYTES;
-    float2 w[9];
-    const float2* src = nullptr;
-    if (valid) {
-      int np = p, ns = s;
-      if (d) {
-        ns = cb_neighbour(ng.g, s, crd, (d - 1) >> 1, (d & 1) ? 1 : -1);
-        np = 1 - p;
-        load_hop_matrix(ng, p, s, d, w);
+    // the MMAs of d - 1 read the operand buffers: wait for them
+    if (d >= 1 && tid == 0 && *s_ok && !mbar_wait(bar, (uint32_t)((d - 1) & 1), WAIT_CYCLES)) *s_ok = 0;
+    __syncthreads();
+
+    // weights of direction d -> B operand (N = output channel c, K = input channel c')
+#pragma unroll
+    for (int i = tid; i < 256; i += 128) {
+      const int c = i >> 4, cp = i & 15;
+      float wv;
+      if (!transpose) {
+        wv = __bfloat162float(W[d * 256 + i]);
+      } else {
+        const int dd = d == 0 ? 0 : ((d & 1) ? d + 1 : d - 1);
+        wv = (d == 0 ? 1.f : -1.f) * __bfloat162float(W[(dd * 16 + cp) * 16 + c]);
       }
-      src = act_ptr(hin, 16, Vh, np, ns) + half * 24;
+      *(__nv_bfloat16*)(tc_smem + L_B + op_offset(c, cp)) = __float2bfloat16_rn(wv);
     }
+
+    const uint32_t rb = base + L_S + (uint32_t)buf * S_BYTES;
     // packed bf16 words of this thread's 8 channels for the six rows: [row][word]
     // (words 0, 1 from channel group g = 0, words 2, 3 from g = 1), hi and lo
     uint32_t hw[6][4], lw[6][4];
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
-      float2 t[4][3];
-      if (valid) {
-        const float4* s4 = (const float4*)(src + g * 12);
-        float2 v[4][3];
+      float2 v[4][3], t[4][3];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-          const float4 u = __ldg(s4 + q);
-          v[(2 * q) / 3][(2 * q) % 3] = make_float2(u.x, u.y);
-          v[(2 * q + 1) / 3][(2 * q + 1) % 3] = make_float2(u.z, u.w);
-        }
+      for (int q = 0; q < 6; ++q) {
+        const float4 u = ld_shared_v4(rb + rec_off(s_local, half * 12 + g * 6 + q));
+        v[(2 * q) / 3][(2 * q) % 3] = make_float2(u.x, u.y);
+        v[(2 * q + 1) / 3][(2 * q + 1) % 3] = make_float2(u.z, u.w);
+      }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          if (d) {
+      for (int c = 0; c < 4; ++c) {
+        if (d) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-              t[c][i] = make_float2(0.f, 0.f);
+          for (int i = 0; i < 3; ++i) {
+            t[c][i] = make_float2(0.f, 0.f);
 #pragma unroll
-              for (int j = 0; j < 3; ++j) cmac(t[c][i], w[3 * i + j], v[c][j]);
-            }
-          } else {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) t[c][i] = v[c][i];
+            for (int j = 0; j < 3; ++j) cmac(t[c][i], w[3 * i + j], v[c][j]);
           }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) t[c][i] = v[c][i];
         }
-      } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int i = 0; i < 3; ++i) t[c][i] = make_float2(0.f, 0.f);
       }
       // rows j * 64 + s_local, j = 2 * colour + (0: re, 1: im); K = half * 8 + g * 4 + 0..3
 #pragma unroll
@@ -279,8 +339,7 @@ __global__ void __launch_bounds__(128, 4)
       }
     }
     // one 16-byte store per row and part: a quarter-warp's eight lanes (eight
-    // consecutive rows of one core matrix) cover 128 contiguous bytes, free of
-    // bank conflicts (two 8-byte stores per row collided four ways)
+    // consecutive rows of one core matrix) cover 128 contiguous bytes
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const uint32_t off = (uint32_t)op_offset(j * TILE + s_local, half * 8);
@@ -291,22 +350,24 @@ __global__ void __launch_bounds__(128, 4)
     __syncthreads();
     if (tid == 0 && *s_ok) {
       tc_fence_after();
-      const uint64_t bdesc = smem_desc(smem_u32(Bw + d * B_BYTES), 128, 256);
+      const uint64_t bdesc = smem_desc(base + L_B, 128, 256);
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const uint32_t dcol = tmem + 16 * b;
         mma_bf16(dcol, smem_desc(hi_base + b * 4096, 128, 256), bdesc, IDESC, d > 0 ? 1u : 0u);
         mma_bf16(dcol, smem_desc(lo_base + b * 4096, 128, 256), bdesc, IDESC, 1u);
       }
-      mma_commit(&bar[buf]);
+      mma_commit(bar);
     }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) w[e] = wn[e];
   }
-  // the last commit (direction 8, buffer 0, its fifth phase) covers every MMA
-  if (tid == 0 && *s_ok && !mbar_wait(&bar[0], 0u, WAIT_CYCLES)) *s_ok = 0;
+  // the commit of direction 8 (the barrier's ninth phase, parity 0) covers every MMA
+  if (tid == 0 && *s_ok && !mbar_wait(bar, 0u, WAIT_CYCLES)) *s_ok = 0;
   __syncthreads();
   tc_fence_after();
   const bool ok = *s_ok != 0;
-  float* E = (float*)tc_smem;  // reuses the operand buffers: [64 sites][E_STRIDE]
+  float* E = (float*)(tc_smem + L_S);  // reuses the record buffers: [64 sites][E_STRIDE]
   if (ok) {
     // warp w holds rows 32 w .. 32 w + 31 of each 128-row block b:
     // colour b, component w / 2 (re, im), sites 32 (w % 2) + lane

@@ -67,12 +67,17 @@ def test_batched_solve_with_each_variant(v):
     f = Field.get(dims)
     b = np.stack([synth.gaussian_source(dims, 5400 + k) for k in range(4)])
     key = stag.stag_tune_key("dslash_mrhs", "fp32", 6, 4, dims)
+    key_epi = stag.stag_tune_key("dslash_mrhs_epi", "fp32", 6, 4, dims)
     try:
         stag.stag_tune_cache_clear()
         stag.stag_tune_cache_put(key, v, 1.0)
+        stag.stag_tune_cache_put(key_epi, v, 1.0)
         h = f.handle(recon=12)
         x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
         infos = stag.stag_batch_solve([(h, x, dev(b), 4, mass)], mode="mixed32", tol=1e-10)
+        assert stag.stag_tuned_mrhs(h, "fp32", 4, epilogue=True)[:2] == VARIANTS[v]
+        assert stag.stag_tuned_mrhs_variant(h, "fp32", 4, epilogue=True) == v
+        assert stag.stag_tuned_mrhs_variant(h, "fp32", 4) == v
         xh = x.cpu().numpy()
         for i in range(4):
             res = oracle_true_residual(f.fat, f.lng, xh[i], b[i], mass, dims)
@@ -90,6 +95,7 @@ def test_tuner_picks_and_remembers():
     dims = (8, 8, 8, 8)
     f = Field.get(dims)
     key = stag.stag_tune_key("dslash_mrhs", "fp32", 6, 4, dims)
+    key_epi = stag.stag_tune_key("dslash_mrhs_epi", "fp32", 6, 4, dims)
     stag.stag_tune_cache_clear()
     try:
         h = f.handle(recon=12, prec_mask=1 << stag.STAG_FP32)
@@ -99,6 +105,10 @@ def test_tuner_picks_and_remembers():
         sp, minb, us = stag.stag_tuned_mrhs(h, "fp32", 4)
         v, us_cached = stag.stag_tune_cache_get(key)
         assert v >= 0 and VARIANTS[v] == (sp, minb) and us > 0 and us_cached == pytest.approx(us, rel=1e-6)
+        # the epilogue form is tuned on its own and cached under its own key
+        spe, minbe, use = stag.stag_tuned_mrhs(h, "fp32", 4, epilogue=True)
+        ve, use_cached = stag.stag_tune_cache_get(key_epi)
+        assert ve >= 0 and VARIANTS[ve] == (spe, minbe) and use > 0 and use_cached == pytest.approx(use, rel=1e-6)
         h2 = f.handle(recon=12, prec_mask=1 << stag.STAG_FP32)
         stag.stag_dslash(h2, out, psi, 1, "fp32", nrhs=4)
         assert stag.stag_tuned_mrhs(h2, "fp32", 4)[:2] == (sp, minb)
