@@ -723,7 +723,7 @@ def run_config(args):
             bd = torch.from_numpy(synth.gaussian_source(dims, 5000 + 100 * j, nrhs=8)).to(dev)
             items.append((h, torch.zeros_like(bd), bd, 8, masses[j % 3]))
         res = {}
-        for mode in ("mixed32", "mixedfx16"):
+        for mode in ("mixed32", "mixedfx16", "mixed16l"):
             def batched():
                 for it in items:
                     it[1].zero_()
