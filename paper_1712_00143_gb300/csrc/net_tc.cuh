@@ -135,13 +135,14 @@ __host__ __device__ __forceinline__ int op_offset(int row, int k) {
   return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-// hi = bf16(x), lo = bf16(x - hi), two values packed per 32-bit word.
+// hi = bf16(x), lo = bf16(x - hi), two values packed per 32-bit word (a in
+// the low half): one packing conversion for each part, the hi values
+// widened back by a shift.
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
-  const __nv_bfloat16 al = __float2bfloat16_rn(a - __bfloat162float(ah));
-  const __nv_bfloat16 bl = __float2bfloat16_rn(b - __bfloat162float(bh));
-  hi = (uint32_t)__bfloat16_as_ushort(ah) | ((uint32_t)__bfloat16_as_ushort(bh) << 16);
-  lo = (uint32_t)__bfloat16_as_ushort(al) | ((uint32_t)__bfloat16_as_ushort(bl) << 16);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
@@ -158,32 +159,35 @@ constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds at GB300 c
 
 // ---- layout of the layer kernel's shared memory (bytes from the 1024-aligned base)
 constexpr int REC = 16 * 3 * 8;                      // one site's 16 input channels: 384 B
-constexpr int REC_CHUNKS = REC / 16;                 // 24 chunks of 16 B
-constexpr int S_BYTES = TILE * REC;                  // one staged direction: 24576 B
+constexpr int REC_STRIDE = REC + 16;                 // staged records 400 B apart (bank groups)
+constexpr int S_BYTES = TILE * REC_STRIDE;           // one staged direction: 25600 B
 constexpr int L_A = 0;                               // A operand, hi and lo parts
 constexpr int L_S = L_A + 2 * A_BYTES;               // staged neighbour records, two directions
 constexpr int L_B = L_S + 2 * S_BYTES;               // B operand of the current direction
-constexpr int L_NB = L_B + B_BYTES;                  // neighbour table int [9][TILE]
-constexpr int L_BAR = L_NB + NET_NDIR * TILE * 4;    // mbarrier, tensor-memory slot, status
-constexpr int LAYER_SMEM = L_BAR + 64;               // 76608 B: three CTAs per SM
+constexpr int L_BAR = L_B + B_BYTES;                 // mbarriers, tensor-memory slot, status
+constexpr int LAYER_SMEM = L_BAR + 64;               // 76352 B: three CTAs per SM
 
 static_assert(TILE * E_STRIDE * 4 <= 2 * S_BYTES, "epilogue staging must fit in the record buffers");
-static_assert(L_S % 16 == 0 && L_B % 16 == 0 && L_BAR % 8 == 0, "alignment");
+static_assert(L_S % 16 == 0 && L_B % 16 == 0 && L_BAR % 8 == 0 && REC_STRIDE % 16 == 0, "alignment");
 
-// Chunk q of staged record r: the low three bits of the chunk index are
-// XORed with the record's, so that eight consecutive records read at one
-// chunk index fall in eight different 16-byte bank groups.
-__device__ __forceinline__ uint32_t rec_off(int r, int q) {
-  return (uint32_t)(r * REC + (((q & ~7) | ((q ^ r) & 7)) << 4));
-}
+// Offset of chunk q (16 B) of staged record r.  Records sit 400 B apart, so
+// eight consecutive records read at one chunk index fall in eight different
+// 16-byte bank groups (25 r + q mod 8).
+__device__ __forceinline__ uint32_t rec_off(int r, int q) { return (uint32_t)(r * REC_STRIDE + q * 16); }
 
-// 16-byte asynchronous copy global -> shared (src_bytes 0: zero fill).
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+// mbarrier arrival that also announces `bytes` of bulk-copy data for the phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bulk copy global -> shared of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned), completion counted on *bar.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ float4 ld_shared_v4(uint32_t addr) {
@@ -200,24 +204,29 @@ __device__ __forceinline__ float4 ld_shared_v4(uint32_t addr) {
 //
 // Per direction d the CTA (64 sites of one parity, 128 threads) needs the
 // 384-byte input records of the 64 neighbour sites.  They are copied into
-// shared memory with 16-byte asynchronous copies one direction ahead (a
-// warp's copies cover 512 contiguous bytes when the neighbours are
-// consecutive sites), so that the gather of d + 1 is in flight while the
-// CUDA cores transport direction d and the tensor cores mix it; the link
-// matrix of d + 1 is prefetched into registers the same way.  The A and B
-// operands are single-buffered: the MMAs of d - 1 (a few hundred cycles)
-// are complete long before the transports of d are, and the smaller
-// footprint lets three CTAs share an SM.  Input activations must be 16-byte
-// aligned (every workspace buffer is).
+// shared memory one direction ahead, one bulk copy per record issued by the
+// record's own site thread of channel half 0 (the copy engine moves the
+// bytes; completion is counted on a per-buffer mbarrier: 64 arrivals, each
+// announcing its 384 bytes; splitting each record between the site's two
+// threads balanced the warps but doubled the neighbour-index work and was
+// slower), so that the gather of d + 1 is in flight while the CUDA cores
+// transport direction d and the tensor cores mix it; the link matrix of
+// d + 1 is prefetched into registers the same way.  The A and B operands
+// are single-buffered: the MMAs of d - 1 (a few hundred cycles) are
+// complete long before the transports of d are, and the smaller footprint
+// lets three CTAs share an SM.  Every wait is bounded; a wait for copies is
+// kept even after an MMA wait gave up, so that no copy is in flight when
+// the CTA leaves.  Input activations must be 16-byte aligned (every
+// workspace buffer is).
 template <bool GATE>
 __global__ void __launch_bounds__(128, 3)
     k_net_layer_tc(NetGeom ng, const float2* __restrict__ hin, float2* __restrict__ pre, float2* __restrict__ hout,
                    const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias, int transpose) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  int* nb = (int*)(tc_smem + L_NB);                        // [9][TILE] neighbour site, -1 past the end
-  uint64_t* bar = (uint64_t*)(tc_smem + L_BAR);
-  uint32_t* tmem_slot = (uint32_t*)(bar + 1);
+  uint64_t* bar = (uint64_t*)(tc_smem + L_BAR);  // MMA completion
+  uint64_t* bar_s = bar + 1;                      // [2] record buffers
+  uint32_t* tmem_slot = (uint32_t*)(bar + 3);
   int* s_ok = (int*)(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -230,14 +239,11 @@ __global__ void __launch_bounds__(128, 3)
   const int s_local = tid & 63, half = tid >> 6;
   const int s = s0 + s_local;
   const bool valid = s < Vh;
-  {
-    const Coord crd = valid ? cb_coords(ng.g, s, p) : Coord{0, 0, 0, 0};
-    for (int d = half ? 5 : 0; d < (half ? NET_NDIR : 5); ++d)
-      nb[d * TILE + s_local] =
-          !valid ? -1 : d == 0 ? s : cb_neighbour(ng.g, s, crd, (d - 1) >> 1, (d & 1) ? 1 : -1);
-  }
+  const Coord crd = valid ? cb_coords(ng.g, s, p) : Coord{0, 0, 0, 0};
   if (tid == 0) {
     mbar_init(bar, 1);
+    mbar_init(&bar_s[0], TILE);
+    mbar_init(&bar_s[1], TILE);
     *s_ok = 1;
     fence_barrier_init();
   }
@@ -250,19 +256,18 @@ __global__ void __launch_bounds__(128, 3)
   const uint32_t base = smem_u32(tc_smem);
   const uint32_t hi_base = base + L_A, lo_base = base + L_A + A_BYTES;
 
-  // the 64 records of direction d -> record buffer b: chunk i = k * 128 + tid
+  // the record of this site's neighbour in direction d -> slot s_local of
+  // record buffer b (threads of half 0; a site past the end only arrives)
   auto stage = [&](int d, int b) {
-    const uint32_t sb = base + L_S + (uint32_t)b * S_BYTES;
-    const char* src0 = (const char*)act_ptr(hin, 16, Vh, d ? 1 - p : p, 0);
-#pragma unroll
-    for (int k = 0; k < TILE * REC_CHUNKS / 128; ++k) {
-      const int i = k * 128 + tid;
-      const int r = i / REC_CHUNKS, q = i - r * REC_CHUNKS;
-      const int ns = nb[d * TILE + r];
-      const char* src = ns >= 0 ? src0 + (size_t)ns * REC + q * 16 : (const char*)hin;
-      cp_async16(sb + rec_off(r, q), src, ns >= 0 ? 16u : 0u);
+    if (half) return;
+    if (valid) {
+      const int ns = d == 0 ? s : cb_neighbour(ng.g, s, crd, (d - 1) >> 1, (d & 1) ? 1 : -1);
+      mbar_arrive_expect_tx(&bar_s[b], (uint32_t)REC);
+      bulk_g2s(base + L_S + (uint32_t)b * S_BYTES + rec_off(s_local, 0), act_ptr(hin, 16, Vh, d ? 1 - p : p, ns),
+               (uint32_t)REC, &bar_s[b]);
+    } else {
+      mbar_arrive(&bar_s[b]);
     }
-    cp_async_commit();
   };
 
   stage(0, 0);
@@ -275,15 +280,18 @@ __global__ void __launch_bounds__(128, 3)
     const int buf = d & 1;
     if (d + 1 < NET_NDIR) {
       // the record buffer of d + 1 was last read by the transports of d - 1,
-      // which every thread finished before the barrier ahead of that MMA
+      // which every thread finished before the barrier ahead of that MMA,
+      // and its barrier's previous phase was waited for in iteration d - 1
       stage(d + 1, buf ^ 1);
       if (valid) load_hop_matrix(ng, p, s, d + 1, wn);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
     }
-    // the MMAs of d - 1 read the operand buffers: wait for them
-    if (d >= 1 && tid == 0 && *s_ok && !mbar_wait(bar, (uint32_t)((d - 1) & 1), WAIT_CYCLES)) *s_ok = 0;
+    if (tid == 0) {
+      // the records of d (phase d / 2 of their buffer's barrier): waited
+      // for whatever happened before, so that no copy outlives the CTA
+      if (!mbar_wait(&bar_s[buf], (uint32_t)((d >> 1) & 1), WAIT_CYCLES)) *s_ok = 0;
+      // the MMAs of d - 1 read the operand buffers: wait for them
+      if (d >= 1 && *s_ok && !mbar_wait(bar, (uint32_t)((d - 1) & 1), WAIT_CYCLES)) *s_ok = 0;
+    }
     __syncthreads();
 
     // weights of direction d -> B operand (N = output channel c, K = input channel c')
