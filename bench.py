@@ -233,9 +233,9 @@ def _oracle_worker_init(names, shape, dtype):
 def _oracle_worker_sample(args):
     import oracle
 
-    b, sample_iters = args
+    b, sample_iters, dims, mass, tol = args
     t = time.perf_counter()
-    oracle.cg(_SHARED["fat"][1], _SHARED["lng"][1], b, MASS, DIMS, tol=TOL, max_iter=sample_iters)
+    oracle.cg(_SHARED["fat"][1], _SHARED["lng"][1], b, mass, dims, tol=tol, max_iter=sample_iters)
     return time.perf_counter() - t
 
 
@@ -273,7 +273,7 @@ class OraclePool:
     def sample(self, srcs, sample_iters):
         """Wall time of `sample_iters` oracle CG iterations on every source at once."""
         t = time.perf_counter()
-        per = self.pool.map(_oracle_worker_sample, [(b, sample_iters) for b in srcs])
+        per = self.pool.map(_oracle_worker_sample, [(b, sample_iters, DIMS, MASS, TOL) for b in srcs])
         return time.perf_counter() - t, per
 
     def close(self):

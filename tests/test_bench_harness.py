@@ -63,3 +63,26 @@ def test_clock_summary_flags_throttling():
     s = c.summary()
     assert s["sm_mhz"] == 1850.0 and s["sm_max_mhz"] == 2070.0
     assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_oracle_cpu_baseline_runs_one_process_per_source():
+    """The CPU baseline's process pool (spawned workers, links in shared
+    memory) on a small lattice: four sources, four workers, a positive
+    per-source time scaled to the requested iteration count, and the same
+    number of iterations timed on every source."""
+    import synth
+
+    dims = (4, 4, 4, 6)
+    fat, lng = synth.gauge_field(dims, 0.3, 1000)
+    srcs = [synth.gaussian_source(dims, 5000 + k) for k in range(4)]
+    old = bench.DIMS
+    bench.DIMS = dims  # the workers receive the parent's lattice with each task
+    try:
+        pool = bench.OraclePool(fat, lng, 4)
+        try:
+            wall, per = pool.sample(srcs, 2)
+        finally:
+            pool.close()
+    finally:
+        bench.DIMS = old
+    assert pool.workers == 4 and len(per) == 4 and all(t > 0 for t in per) and wall > 0
