@@ -232,8 +232,8 @@ static int net_run_init(stag_net_s* net, stag_lattice_s* lat, NetRun& R, bool tr
 }
 
 template <int CIN, int COUT, bool GATE>
-static void launch_layer(const NetRun& R, int l, const float2* in, float2* pre, float2* out, const __nv_bfloat16* W,
-                         const float* b, int transpose, cudaStream_t st) {
+static int launch_layer(const NetRun& R, int l, const float2* in, float2* pre, float2* out, const __nv_bfloat16* W,
+                        const float* b, int transpose, cudaStream_t st) {
   const int n = 2 * R.Vh;
   count_launch();
   if constexpr (CIN == 16 && COUT == 16) {
@@ -244,6 +244,8 @@ static void launch_layer(const NetRun& R, int l, const float2* in, float2* pre, 
       cudaFuncSetAttribute(k_net_layer_tc<GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::LAYER_SMEM);
       attr[GATE] = true;
     }
+    // the layer's bulk copies need 16-byte aligned input records
+    if (((uintptr_t)in & 15u) != 0) return STAG_EINVAL;
     const int tiles = 2 * ((R.Vh + tc::TILE - 1) / tc::TILE);
     k_net_layer_tc<GATE><<<tiles, 128, tc::LAYER_SMEM, st>>>(R.ng, in, pre, out, W, b, transpose);
   } else if constexpr (COUT == 1 && CIN == 16 && !GATE) {
@@ -266,6 +268,7 @@ static void launch_layer(const NetRun& R, int l, const float2* in, float2* pre, 
     }
     k_net_layer<CIN, COUT, GATE><<<(n + 127) / 128, 128, smem, st>>>(R.ng, in, pre, out, W, b, transpose);
   }
+  return STAG_OK;
 }
 
 // STAG_ETIMEOUT if a tensor-core layer gave up a bounded wait since the
@@ -294,11 +297,13 @@ static int layer_fwd(const NetRun& R, int l, cudaStream_t st) {
   const float* b = gate ? N->w + N->boff[l] : nullptr;
   float2 *in = R.h[l], *out = R.h[l + 1], *pre = gate ? R.pre[l + 1] : R.h[l + 1];
   ProfScope ps(ci == 16 && co == 16 ? "net_tc" : "net", st);
-  if (ci == 1 && co == 16 && gate) launch_layer<1, 16, true>(R, l, in, pre, out, W, b, 0, st);
-  else if (ci == 16 && co == 16 && gate) launch_layer<16, 16, true>(R, l, in, pre, out, W, b, 0, st);
-  else if (ci == 16 && co == 1 && !gate) launch_layer<16, 1, false>(R, l, in, pre, out, W, b, 0, st);
-  else if (ci == 1 && co == 1 && !gate) launch_layer<1, 1, false>(R, l, in, pre, out, W, b, 0, st);
+  int ls;
+  if (ci == 1 && co == 16 && gate) ls = launch_layer<1, 16, true>(R, l, in, pre, out, W, b, 0, st);
+  else if (ci == 16 && co == 16 && gate) ls = launch_layer<16, 16, true>(R, l, in, pre, out, W, b, 0, st);
+  else if (ci == 16 && co == 1 && !gate) ls = launch_layer<16, 1, false>(R, l, in, pre, out, W, b, 0, st);
+  else if (ci == 1 && co == 1 && !gate) ls = launch_layer<1, 1, false>(R, l, in, pre, out, W, b, 0, st);
   else return STAG_EINVAL;
+  if (ls) return ls;
   return last_launch_status();
 }
 
@@ -346,11 +351,13 @@ static int layer_bwd(const NetRun& R, int l, float2* g, float2* gin, bool want_i
     // adjoint layer: co -> ci channels with W' (transposed, partner directions, sign)
     ProfScope ps("net_bwd", st);
     const __nv_bfloat16* W = N->wb + N->woff[l];
-    if (ci == 16 && co == 16) launch_layer<16, 16, false>(R, l, g, gin, gin, W, nullptr, 1, st);
-    else if (ci == 16 && co == 1) launch_layer<1, 16, false>(R, l, g, gin, gin, W, nullptr, 1, st);
-    else if (ci == 1 && co == 16) launch_layer<16, 1, false>(R, l, g, gin, gin, W, nullptr, 1, st);
-    else if (ci == 1 && co == 1) launch_layer<1, 1, false>(R, l, g, gin, gin, W, nullptr, 1, st);
+    int ls;
+    if (ci == 16 && co == 16) ls = launch_layer<16, 16, false>(R, l, g, gin, gin, W, nullptr, 1, st);
+    else if (ci == 16 && co == 1) ls = launch_layer<1, 16, false>(R, l, g, gin, gin, W, nullptr, 1, st);
+    else if (ci == 1 && co == 16) ls = launch_layer<16, 1, false>(R, l, g, gin, gin, W, nullptr, 1, st);
+    else if (ci == 1 && co == 1) ls = launch_layer<1, 1, false>(R, l, g, gin, gin, W, nullptr, 1, st);
     else return STAG_EINVAL;
+    TRYN(ls);
     TRYN(last_launch_status());
   }
   return STAG_OK;

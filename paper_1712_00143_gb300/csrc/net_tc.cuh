@@ -270,10 +270,28 @@ __global__ void __launch_bounds__(128, 3)
     }
   };
 
+  // this thread's two weights of direction d (B operand entries tid and
+  // tid + 128: output channel c, input channel c'), read one direction ahead
+  auto load_weights = [&](int d, __nv_bfloat16 (&wb)[2]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int i = tid + 128 * k, c = i >> 4, cp = i & 15;
+      if (!transpose) {
+        wb[k] = W[d * 256 + i];
+      } else {
+        const int dd = d == 0 ? 0 : ((d & 1) ? d + 1 : d - 1);
+        const float wv = __bfloat162float(W[(dd * 16 + cp) * 16 + c]);
+        wb[k] = __float2bfloat16_rn(d == 0 ? wv : -wv);  // exact: a sign change
+      }
+    }
+  };
+
   stage(0, 0);
   float2 w[9], wn[9];
 #pragma unroll
   for (int e = 0; e < 9; ++e) w[e] = wn[e] = make_float2(0.f, 0.f);
+  __nv_bfloat16 wcur[2], wnext[2] = {__float2bfloat16_rn(0.f), __float2bfloat16_rn(0.f)};
+  load_weights(0, wcur);
 
 #pragma unroll 1
   for (int d = 0; d < NET_NDIR; ++d) {
@@ -284,6 +302,7 @@ __global__ void __launch_bounds__(128, 3)
       // and its barrier's previous phase was waited for in iteration d - 1
       stage(d + 1, buf ^ 1);
       if (valid) load_hop_matrix(ng, p, s, d + 1, wn);
+      load_weights(d + 1, wnext);
     }
     if (tid == 0) {
       // the records of d (phase d / 2 of their buffer's barrier): waited
@@ -296,16 +315,9 @@ __global__ void __launch_bounds__(128, 3)
 
     // weights of direction d -> B operand (N = output channel c, K = input channel c')
 #pragma unroll
-    for (int i = tid; i < 256; i += 128) {
-      const int c = i >> 4, cp = i & 15;
-      float wv;
-      if (!transpose) {
-        wv = __bfloat162float(W[d * 256 + i]);
-      } else {
-        const int dd = d == 0 ? 0 : ((d & 1) ? d + 1 : d - 1);
-        wv = (d == 0 ? 1.f : -1.f) * __bfloat162float(W[(dd * 16 + cp) * 16 + c]);
-      }
-      *(__nv_bfloat16*)(tc_smem + L_B + op_offset(c, cp)) = __float2bfloat16_rn(wv);
+    for (int k = 0; k < 2; ++k) {
+      const int i = tid + 128 * k;
+      *(__nv_bfloat16*)(tc_smem + L_B + op_offset(i >> 4, i & 15)) = wcur[k];
     }
 
     const uint32_t rb = base + L_S + (uint32_t)buf * S_BYTES;
@@ -369,6 +381,8 @@ __global__ void __launch_bounds__(128, 3)
     }
 #pragma unroll
     for (int e = 0; e < 9; ++e) w[e] = wn[e];
+    wcur[0] = wnext[0];
+    wcur[1] = wnext[1];
   }
   // the commit of direction 8 (the barrier's ninth phase, parity 0) covers every MMA
   if (tid == 0 && *s_ok && !mbar_wait(bar, 0u, WAIT_CYCLES)) *s_ok = 0;
