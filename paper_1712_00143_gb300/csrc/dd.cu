@@ -313,6 +313,9 @@ int stag_dd_cg(stag_dd_t d, void* x, const void* b, double mass, const stag_solv
       }
       TRYD(cuda_status(cudaMemcpyAsync(&h, dst, sizeof(CgState), cudaMemcpyDeviceToHost, st)));
       TRYD(cuda_status(cudaStreamSynchronize(st)));
+      // the iterations that did work: after a stop flag the rest of the chunk
+      // returned at once and left the device's count where it was
+      iters = h.iter;
       if (h.flags & F_BREAKDOWN) {
         status = STAG_EBREAKDOWN;
         break;
