@@ -158,12 +158,14 @@ def test_split_cg_reaches_the_oracle_residual(field, nranks):
     resid = oracle_true_residual(fat, lng, x, b, mass, GDIMS)
     print(f"split CG on {nranks} ranks: {infos[0]['iters']} iterations, oracle residual {resid:.2e}")
     assert resid <= 1e-10
-    # the single-lattice FP64 CG takes the same iterations to within a check interval
+    # the single-lattice FP64 CG takes the same iterations (to within the
+    # rounding of sums taken in a different order)
     h = stag.stag_load_links(GDIMS, dev(fat), dev(lng))
     xs = torch.zeros((h.Vh, 3), dtype=torch.complex128, device="cuda")
     single = stag.stag_cg(h, xs, dev(b), mass, mode="plain64", tol=1e-10)
     h.free()
-    assert abs(single["iters"] - infos[0]["iters"]) <= 16, (single["iters"], infos[0]["iters"])
+    print(f"single-lattice FP64 CG: {single['iters']} iterations")
+    assert abs(single["iters"] - infos[0]["iters"]) <= 2, (single["iters"], infos[0]["iters"])
 
 
 def _free_port():
