@@ -130,11 +130,13 @@ def test_batch_full_workload_12_lattices():
     print(f"batched 96 systems on 12 lattices: {el:.3f} s")
 
 
-def test_batch_headline_workload_32_4_four_sources():
-    """The bench's chosen form exactly: 32^4, m = 0.01, the four seeded
-    Gaussian sources in one stag_batch_solve call (mixed32, one group of
-    four, double-float reliable updates), every solution judged by the
-    oracle's FP64 true residual over the whole field."""
+@pytest.mark.parametrize("mode", ["mixed32", "mixed16l"])
+def test_batch_headline_workload_32_4_four_sources(mode):
+    """The bench's chosen form exactly (mixed32), and its fixed-point-link
+    alternative (mixed16l): 32^4, m = 0.01, the four seeded Gaussian
+    sources in one stag_batch_solve call (one group of four, double-float
+    reliable updates), every solution judged by the oracle's FP64 true
+    residual over the whole field."""
     stag = _stag()
     dims, mass = (32, 32, 32, 32), 0.01
     fat, lng = synth.gauge_field(dims, 0.3, 1000)
@@ -142,7 +144,7 @@ def test_batch_headline_workload_32_4_four_sources():
     b = np.stack([synth.gaussian_source(dims, 5000 + k) for k in range(4)])
     bd = dev(b)
     x = torch.zeros_like(bd)
-    infos = stag.stag_batch_solve([(h, x, bd, 4, mass)], mode="mixed32", tol=1e-10)
+    infos = stag.stag_batch_solve([(h, x, bd, 4, mass)], mode=mode, tol=1e-10)
     xh = x.cpu().numpy()
     h.free()
     for i in range(4):
